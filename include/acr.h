@@ -1,0 +1,150 @@
+/*
+ * acr.h -- C ABI of the GB300 block cyclic reduction solver (Accelerated
+ * Cyclic Reduction, Chavez, Turkiyyah & Keyes, "A Direct Elliptic Solver Based
+ * on Hierarchically Low-rank Schur Complements").
+ *
+ * The solver handles a block tridiagonal system  M u = f,
+ *
+ *     M = tridiag(A_i, D_i, C_i),   i = 0 .. nblk-1,  blocks blksz x blksz,
+ *
+ * (Section 3, the block tridiagonal form of the 2D operator; the paper names
+ * the off-diagonal blocks E_i and F_i, here A_i = E_i is the sub-diagonal
+ * block of row i and C_i = F_i the super-diagonal one).  acr_factor runs the
+ * reduction phase of block cyclic reduction (Section 3: even/odd permutation,
+ * block-wise inversion of the eliminated diagonal blocks, Schur complement of
+ * Eq. "fund", recursion down to one block) and keeps every level's factors
+ * resident on the GPU; acr_solve runs the forward right-hand-side reduction
+ * (f^(1) = f_odd - H21 H11^-1 f_even, Eq. "fund") and the back-substitution.
+ *
+ * Conventions common to every call
+ *  - Blocks are column-major (element (r, c) of a block at r + c*blksz) and
+ *    the nblk blocks of each of A, D, C are contiguous (block stride
+ *    blksz*blksz).  A[0] and C[nblk-1] are never read.
+ *  - Right-hand sides B are N x nrhs column-major with leading dimension
+ *    N = nblk*blksz, in natural block order.
+ *  - Every pointer may be host or device memory; the library detects which
+ *    (cudaPointerGetAttributes).  The caller keeps ownership of its buffers
+ *    and may free them as soon as the call returns; the library copies what
+ *    it keeps.
+ *  - Every call is synchronous with respect to the host: when it returns, the
+ *    work it queued on its stream has finished (results are in B).
+ *  - Every call returns an acr_status.  On failure nothing is leaked, *out is
+ *    set to NULL, and acr_last_error() describes the failure (for a singular
+ *    block: the reduction level and the block index at that level).
+ *  - One GPU: the current CUDA device at acr_factor time is used for the
+ *    lifetime of the handle.
+ */
+#ifndef ACR_H
+#define ACR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acr_ctx *acr_handle; /* opaque; owned by the library */
+
+enum acr_status {
+    ACR_OK = 0,
+    ACR_ERR_INVALID_ARG = -1,   /* bad size, NULL pointer, NaN/Inf in input */
+    ACR_ERR_OOM = -2,           /* device allocation failed / over budget */
+    ACR_ERR_SINGULAR = -3,      /* an eliminated block has a zero pivot */
+    ACR_ERR_NOT_CONVERGED = -4, /* refinement missed ir_tol in ir_max_iter */
+    ACR_ERR_CUDA = -5,          /* a CUDA call failed */
+    ACR_ERR_TIMEOUT = -6        /* a bounded device-side wait gave up */
+};
+
+enum acr_precision {
+    /* every step in FP64 (the plain GPU FP64 path) */
+    ACR_FP64 = 0,
+    /* factor and sweeps in FP32 with the block products on TF32 tensor cores
+     * (three-term split, FP32-accurate), wrapped in iterative refinement whose
+     * residual r = f - M x (original operator) and correction x += d are FP64 */
+    ACR_FP32TC_IR = 1,
+    /* as ACR_FP32TC_IR but the block products on FP32 CUDA cores */
+    ACR_FP32_IR = 2
+};
+
+enum acr_input_kind {
+    /* A, D, C: nblk dense blksz x blksz blocks each (layout above) */
+    ACR_DENSE = 0,
+    /* compact form of a 5-point stencil: D holds 3*blksz values per block,
+     * [sub-diagonal, diagonal, super-diagonal] of the tridiagonal D_i
+     * (sub[0] and super[blksz-1] ignored); A and C hold blksz values per block,
+     * the diagonals of the diagonal blocks A_i and C_i (Section 3: D_i is
+     * tridiagonal, E_i and F_i are diagonal) */
+    ACR_BANDED = 1
+};
+
+typedef struct {
+    int precision;      /* enum acr_precision, default ACR_FP64 */
+    int input_kind;     /* enum acr_input_kind, default ACR_DENSE */
+    int leaf;           /* HODLR leaf size for tol > 0 (0: library choice) */
+    int max_rank;       /* cap on HODLR off-diagonal ranks (0: none) */
+    int m_stop;         /* stop the reduction at this many blocks; 1 only */
+    double ir_tol;      /* refinement target ||f - M x||_2 / ||f||_2 per column
+                           (default 1e-8) */
+    int ir_max_iter;    /* refinement iteration cap (default 20) */
+    void *stream;       /* cudaStream_t to run on; NULL: a library stream */
+} acr_opts;
+
+/* Fill *o with the defaults listed above. */
+void acr_default_opts(acr_opts *o);
+
+/* Factor (reduction phase of Section 3) with default options.
+ *  nblk, blksz >= 1.  tol <= 0: uncompressed blocks (dense block cyclic
+ *  reduction, FP64).  tol > 0: blocks stored in HODLR form with off-diagonal
+ *  ranks truncated at sigma_k > tol * sigma_1 of each node.
+ *  On success *out receives a handle that keeps the factorization on the GPU
+ *  until acr_free. */
+int acr_factor(int nblk, int blksz, const double *A, const double *D, const double *C,
+               double tol, acr_handle *out);
+
+/* As acr_factor with explicit options (o may be NULL for the defaults). */
+int acr_factor_ex(int nblk, int blksz, const double *A, const double *D, const double *C,
+                  double tol, const acr_opts *o, acr_handle *out);
+
+/* Solve M X = B in place (forward reduction + back-substitution of Section 3,
+ * refinement in the mixed-precision modes).  B: N x nrhs, overwritten with X.
+ * nrhs >= 0.  Solves on one handle may run concurrently from several host
+ * threads: each call uses its own workspace. */
+int acr_solve(acr_handle h, double *B, int nrhs);
+
+/* As acr_solve, also returning per column the final relative residual
+ * ||b - M x||_2 / ||b||_2 (resid_out, nrhs doubles, may be NULL; computed in
+ * FP64 with the original operator) and the refinement iterations taken
+ * (iters_out, may be NULL; 0 when no refinement ran). */
+int acr_solve_ex(acr_handle h, double *B, int nrhs, double *resid_out, int *iters_out);
+
+/* Release everything the handle holds.  NULL is a no-op. */
+void acr_free(acr_handle h);
+
+typedef struct {
+    int nblk, blksz, levels, precision, compressed;
+    size_t factor_bytes;     /* device bytes held by the factorization */
+    size_t operator_bytes;   /* device bytes of the FP64 operator copy */
+    double factor_flops;     /* algorithmic flops of the last factor */
+    double factor_ms;        /* device time of the last factor */
+    double solve_ms;         /* device time of the last solve (all iterations) */
+    int ir_iters;            /* refinement iterations of the last solve */
+    double ir_resid_max;     /* max relative residual over columns, last solve */
+    int rank_max[32];        /* HODLR: max off-diagonal rank per level */
+    double rank_mean[32];    /* HODLR: mean off-diagonal rank per level */
+} acr_stats_t;
+
+/* Copy the handle's statistics into *s. */
+int acr_stats(acr_handle h, acr_stats_t *s);
+
+/* Device bytes that acr_factor_ex would keep for these sizes and options
+ * (uncompressed storage; an upper bound when tol > 0).  Used for admission
+ * under a memory budget. */
+int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts *o, size_t *bytes);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *acr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACR_H */

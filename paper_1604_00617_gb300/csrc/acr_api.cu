@@ -1,0 +1,727 @@
+// acr_api.cu -- the C ABI (include/acr.h): handles, the level plan, the
+// reduction (factor) loop, the solve sweeps and FP64 iterative refinement.
+//
+// Factor (Section 3, reduction phase), per level t with m blocks:
+//   1. invert the eliminated blocks D_j, j = 0, 2, 4, ... in place
+//      (block-diagonal H11 inverted block by block);
+//   2. XA_j = D_j^-1 A_j,  XC_j = D_j^-1 C_j;
+//   3. Schur complement (Eq. "fund") on the kept blocks i = 2k+1:
+//        D'_k = D_i - A_i XC_{i-1} - C_i XA_{i+1}
+//        A'_k = -A_i XA_{i-1},   C'_k = -C_i XC_{i+1}
+//      terms whose blocks do not exist are dropped; the result is again block
+//      tridiagonal with floor(m/2) blocks.
+// The recursion ends at one block, which is inverted.  Kept per level for the
+// solve: D_j^-1, XA_j, XC_j (eliminated) and A_i, C_i (kept).
+//
+// Solve: forward, per level, g_j = D_j^-1 f_j and
+//   f'_k = f_i - A_i g_{i-1} - C_i g_{i+1}   (f^(1) of Eq. "fund");
+// top: u = D^-1 f; back-substitution, levels in reverse:
+//   u_j = g_j - XA_j u_{j-1} - XC_j u_{j+1}  (= D_j^-1 (f_j - A_j u_{j-1} - C_j u_{j+1})).
+//
+// Memory layout in HBM: per level, five contiguous arrays of blksz x blksz
+// column-major blocks (D^-1, XA, XC for the ceil(m/2) eliminated blocks;
+// A, C for the floor(m/2) kept blocks).  Level vectors are (m*blksz) x nrhs
+// column-major panels; level 0 is the caller's right-hand side.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/acr.h"
+#include "acr_internal.h"
+
+using namespace acr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            if (e_ == cudaErrorMemoryAllocation) {                                        \
+                cudaGetLastError();                                                       \
+                return fail(ACR_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));        \
+            }                                                                             \
+            return fail(ACR_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                              \
+        }                                                                                 \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Level {
+    int m = 0, ne = 0, nk = 0;
+    size_t off_dinv = 0, off_xa = 0, off_xc = 0, off_ak = 0, off_ck = 0;  // bytes in arena
+};
+
+// Device memory owned by one call or handle; freed on scope exit.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    bool async = false;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) {
+            if (async) cudaFreeAsync(p, s);
+            else cudaFree(p);
+            p = nullptr;
+        }
+    }
+    cudaError_t alloc(size_t bytes, cudaStream_t st) {
+        release();
+        s = st;
+        async = true;
+        if (bytes == 0) bytes = 16;
+        return cudaMallocAsync(&p, bytes, st);
+    }
+    cudaError_t alloc_sync(size_t bytes) {
+        release();
+        async = false;
+        if (bytes == 0) bytes = 16;
+        return cudaMalloc(&p, bytes);
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+struct acr_ctx {
+    int n = 0, b = 0, prec = ACR_FP64, in_kind = ACR_DENSE;
+    double tol = 0.0;
+    acr_opts opts{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t es = 8;  // factor element size
+    std::vector<Level> lev;
+    DevBuf arena;   // persistent factors
+    DevBuf op;      // FP64 copy of the original operator (refinement / residual)
+    std::mutex mu;
+    acr_stats_t st{};
+    ~acr_ctx() {
+        arena.release();
+        op.release();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+    size_t bb() const { return (size_t)b * b; }
+    template <class T> T* P(size_t off) const { return reinterpret_cast<T*>(static_cast<char*>(arena.p) + off); }
+    int levels() const { return (int)lev.size(); }
+};
+
+namespace {
+
+void default_opts(acr_opts* o) {
+    memset(o, 0, sizeof(*o));
+    o->precision = ACR_FP64;
+    o->input_kind = ACR_DENSE;
+    o->leaf = 0;
+    o->max_rank = 0;
+    o->m_stop = 1;
+    o->ir_tol = 1e-8;
+    o->ir_max_iter = 20;
+    o->stream = nullptr;
+}
+
+// Level plan and persistent byte offsets.  Returns the arena size.
+size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev) {
+    lev.clear();
+    const size_t blk = (size_t)b * b * es;
+    size_t off = 0;
+    int m = n;
+    while (true) {
+        Level L;
+        L.m = m;
+        L.ne = (m + 1) / 2;
+        L.nk = m / 2;
+        const bool top = (m == 1);
+        L.off_dinv = off; off += L.ne * blk;
+        L.off_xa = off; off += top ? 0 : L.ne * blk;
+        L.off_xc = off; off += top ? 0 : L.ne * blk;
+        L.off_ak = off; off += L.nk * blk;
+        L.off_ck = off; off += L.nk * blk;
+        lev.push_back(L);
+        if (top) break;
+        m = m / 2;
+    }
+    return off;
+}
+
+double factor_flops(const std::vector<Level>& lev, int b) {
+    // algorithmic flops of dense block cyclic reduction: 2 b^3 per block
+    // inverse, 2 b^3 per block product (D' has two)
+    const double b3 = (double)b * b * b;
+    double f = 0.0;
+    for (size_t t = 0; t < lev.size(); ++t) {
+        const Level& L = lev[t];
+        f += 2.0 * b3 * L.ne;
+        if (L.m == 1) continue;
+        int nxa = 0, nxc = 0;
+        for (int e = 0; e < L.ne; ++e) {
+            if (2 * e > 0) ++nxa;
+            if (2 * e + 1 < L.m) ++nxc;
+        }
+        f += 2.0 * b3 * (nxa + nxc);
+        for (int k = 0; k < L.nk; ++k) {
+            const int i = 2 * k + 1;
+            f += 2.0 * b3 * (1 + (i + 1 < L.m));
+            if (i >= 3) f += 2.0 * b3;
+            if (i + 2 < L.m) f += 2.0 * b3;
+        }
+    }
+    return f;
+}
+
+template <class T>
+int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
+    const int n = h->n, b = h->b;
+    const size_t bb = h->bb(), blk = bb * sizeof(T);
+    cudaStream_t s = h->stream;
+    const bool banded = h->in_kind == ACR_BANDED;
+
+    // ---- stage the input on the device (FP64) ---------------------------
+    const size_t nA = banded ? (size_t)n * b : (size_t)n * bb;
+    const size_t nD = banded ? (size_t)n * 3 * b : (size_t)n * bb;
+    DevBuf sA, sD, sC;
+    const double *dA = A, *dD = D, *dC = C;
+    // A and C are never read when there is a single block
+    if (n > 1 && !is_device_ptr(A)) { CK(sA.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sA.p, A, nA * 8, cudaMemcpyHostToDevice, s)); dA = sA.as<double>(); }
+    if (!is_device_ptr(D)) { CK(sD.alloc(nD * 8, s)); CK(cudaMemcpyAsync(sD.p, D, nD * 8, cudaMemcpyHostToDevice, s)); dD = sD.as<double>(); }
+    if (n > 1 && !is_device_ptr(C)) { CK(sC.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sC.p, C, nA * 8, cudaMemcpyHostToDevice, s)); dC = sC.as<double>(); }
+    if (n == 1) { dA = nullptr; dC = nullptr; }
+
+    // ---- FP64 operator copy (residual of the refinement) -----------------
+    if (banded) {
+        const size_t N = (size_t)n * b;
+        CK(h->op.alloc_sync(5 * N * 8));
+        double* o = h->op.as<double>();
+        // Dl, Dd, Du de-interleaved from [sub, diag, super] per block
+        for (int d = 0; d < 3; ++d)
+            CK(cudaMemcpy2DAsync(o + d * N, b * 8, dD + d * b, 3 * b * 8, b * 8, n, cudaMemcpyDeviceToDevice, s));
+        if (n > 1) {
+            CK(cudaMemcpyAsync(o + 3 * N, dA, N * 8, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(o + 4 * N, dC, N * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        // A_0 and C_{n-1} do not exist: zero them in the copy
+        CK(cudaMemsetAsync(o + 3 * N, 0, b * 8, s));
+        CK(cudaMemsetAsync(o + 4 * N + (N - b), 0, b * 8, s));
+        h->st.operator_bytes = 5 * N * 8;
+    } else {
+        CK(h->op.alloc_sync(3 * (size_t)n * bb * 8));
+        double* o = h->op.as<double>();
+        if (n > 1) {
+            CK(cudaMemcpyAsync(o, dA, (size_t)n * bb * 8, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(o + 2 * (size_t)n * bb, dC, (size_t)n * bb * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        CK(cudaMemcpyAsync(o + (size_t)n * bb, dD, (size_t)n * bb * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(o, 0, bb * 8, s));
+        CK(cudaMemsetAsync(o + 2 * (size_t)n * bb + (size_t)(n - 1) * bb, 0, bb * 8, s));
+        h->st.operator_bytes = 3 * (size_t)n * bb * 8;
+    }
+
+    // ---- persistent arena -------------------------------------------------
+    const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev);
+    CK(h->arena.alloc_sync(arena_bytes));
+    h->st.factor_bytes = arena_bytes;
+    const int T_ = h->levels() - 1;
+
+    // ---- temporaries: D_odd, A_even, C_even per level (ping-pong) ---------
+    auto temp_blocks = [&](const Level& L) { return (size_t)L.nk + 2 * (size_t)L.ne; };
+    size_t tmax[2] = {0, 0};
+    for (int t = 0; t <= T_; ++t) tmax[t & 1] = std::max(tmax[t & 1], temp_blocks(h->lev[t]));
+    DevBuf tmp[2];
+    CK(tmp[0].alloc(tmax[0] * blk, s));
+    CK(tmp[1].alloc(tmax[1] * blk, s));
+    auto t_dodd = [&](int t) { return tmp[t & 1].as<T>(); };
+    auto t_aev = [&](int t) { return tmp[t & 1].as<T>() + (size_t)h->lev[t].nk * bb; };
+    auto t_cev = [&](int t) { return t_aev(t) + (size_t)h->lev[t].ne * bb; };
+
+    // ---- info / pivots / bad flag ------------------------------------------
+    std::vector<int> info_off(T_ + 1);
+    int ninfo = 0, maxne = 0;
+    for (int t = 0; t <= T_; ++t) { info_off[t] = ninfo; ninfo += h->lev[t].ne; maxne = std::max(maxne, h->lev[t].ne); }
+    DevBuf dinfo, dpiv;
+    CK(dinfo.alloc((ninfo + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(dinfo.p, 0, (ninfo + 1) * sizeof(int), s));
+    CK(dpiv.alloc((size_t)maxne * b * sizeof(int), s));
+    int* d_bad = dinfo.as<int>() + ninfo;
+
+    // ---- problem tables (built on the host, one upload) --------------------
+    std::vector<GemmProb<T>> probs;
+    std::vector<size_t> g1_off(T_ + 1), g1_cnt(T_ + 1), g2_off(T_ + 1), g2_cnt(T_ + 1);
+    for (int t = 0; t < T_; ++t) {
+        const Level& L = h->lev[t];
+        const Level& Ln = h->lev[t + 1];
+        T* dinv = h->P<T>(L.off_dinv);
+        T* xa = h->P<T>(L.off_xa);
+        T* xc = h->P<T>(L.off_xc);
+        T* ak = h->P<T>(L.off_ak);
+        T* ck = h->P<T>(L.off_ck);
+        g1_off[t] = probs.size();
+        for (int e = 0; e < L.ne; ++e) {
+            const int j = 2 * e;
+            if (j > 0) probs.push_back({xa + e * bb, nullptr, {dinv + e * bb, nullptr}, {t_aev(t) + e * bb, nullptr}, T(1), T(0)});
+            if (j + 1 < L.m) probs.push_back({xc + e * bb, nullptr, {dinv + e * bb, nullptr}, {t_cev(t) + e * bb, nullptr}, T(1), T(0)});
+        }
+        g1_cnt[t] = probs.size() - g1_off[t];
+        g2_off[t] = probs.size();
+        T* ndinv = h->P<T>(Ln.off_dinv);
+        T* nak = h->P<T>(Ln.off_ak);
+        T* nck = h->P<T>(Ln.off_ck);
+        for (int k = 0; k < L.nk; ++k) {
+            const int i = 2 * k + 1;
+            const bool kev = (k % 2) == 0;
+            const int ks = k / 2;
+            T* Di = t_dodd(t) + k * bb;
+            T* Ai = ak + k * bb;
+            T* Ci = ck + k * bb;
+            GemmProb<T> pd{kev ? ndinv + ks * bb : t_dodd(t + 1) + ks * bb, Di, {Ai, nullptr}, {xc + k * bb, nullptr}, T(-1), T(1)};
+            if (i + 1 < L.m) { pd.a[1] = Ci; pd.bm[1] = xa + (k + 1) * bb; }
+            probs.push_back(pd);
+            if (i >= 3)
+                probs.push_back({kev ? t_aev(t + 1) + ks * bb : nak + ks * bb, nullptr, {Ai, nullptr}, {xa + k * bb, nullptr}, T(-1), T(0)});
+            if (i + 2 < L.m)
+                probs.push_back({kev ? t_cev(t + 1) + ks * bb : nck + ks * bb, nullptr, {Ci, nullptr}, {xc + (k + 1) * bb, nullptr}, T(-1), T(0)});
+        }
+        g2_cnt[t] = probs.size() - g2_off[t];
+    }
+    DevBuf dprobs;
+    CK(dprobs.alloc(std::max<size_t>(1, probs.size()) * sizeof(GemmProb<T>), s));
+    if (!probs.empty())
+        CK(cudaMemcpyAsync(dprobs.p, probs.data(), probs.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice, s));
+    const GemmProb<T>* dp = dprobs.as<GemmProb<T>>();
+
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+
+    // ---- level 0 staging -----------------------------------------------------
+    {
+        const Level& L = h->lev[0];
+        CK(stage_level0<T>(banded ? 1 : 0, n, b, dA, dD, dC, h->P<T>(L.off_dinv), t_dodd(0), t_aev(0),
+                           h->P<T>(L.off_ak), t_cev(0), h->P<T>(L.off_ck), d_bad, s));
+    }
+    const int use_tc = (h->prec == ACR_FP32TC_IR) ? 1 : 0;
+    // ---- the reduction ---------------------------------------------------------
+    for (int t = 0; t <= T_; ++t) {
+        const Level& L = h->lev[t];
+        CK(gj_inverse<T>(h->P<T>(L.off_dinv), b, L.ne, dinfo.as<int>() + info_off[t], dpiv.as<int>(), s));
+        if (t == T_) break;
+        CK(gemm_batched<T>(dp + g1_off[t], (int)g1_cnt[t], b, use_tc, s));
+        CK(gemm_batched<T>(dp + g2_off[t], (int)g2_cnt[t], b, use_tc, s));
+    }
+    CK(cudaEventRecord(e1, s));
+    std::vector<int> info(ninfo + 1);
+    CK(cudaMemcpyAsync(info.data(), dinfo.p, (ninfo + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info[ninfo]) return fail(ACR_ERR_INVALID_ARG, "input holds a NaN or Inf");
+    for (int t = 0; t <= T_; ++t)
+        for (int e = 0; e < h->lev[t].ne; ++e)
+            if (info[info_off[t] + e])
+                return fail(ACR_ERR_SINGULAR, "singular eliminated block: level %d, block %d (pivot %d)", t, 2 * e,
+                            info[info_off[t] + e] - 1);
+    h->st.factor_ms = ms;
+    h->st.factor_flops = factor_flops(h->lev, b);
+    return ACR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve sweeps on a device panel F0 (N x nrhs, ld N, element T), in place.
+// ---------------------------------------------------------------------------
+template <class T>
+struct SweepPlan {
+    DevBuf ws;       // level vectors F_t (t >= 1) and G_t
+    DevBuf dprobs;
+    std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
+    int nrhs = 0;
+};
+
+template <class T>
+int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
+    const int b = h->b, T_ = h->levels() - 1;
+    const size_t bb = h->bb();
+    cudaStream_t s = h->stream;
+    std::vector<size_t> foff(T_ + 1), goff(T_ + 1);
+    size_t tot = 0;
+    for (int t = 0; t <= T_; ++t) {
+        const Level& L = h->lev[t];
+        foff[t] = tot;
+        if (t > 0) tot += (size_t)L.m * b * nrhs;
+        goff[t] = tot;
+        tot += (size_t)L.ne * b * nrhs;
+    }
+    CK(sp.ws.alloc(tot * sizeof(T), s));
+    T* base = sp.ws.template as<T>();
+    auto Fp = [&](int t) { return t == 0 ? F0 : base + foff[t]; };
+    auto Gp = [&](int t) { return base + goff[t]; };
+    std::vector<SweepProb<T>> pr;
+    sp.fw_g_off.assign(T_ + 1, 0); sp.fw_g_cnt.assign(T_ + 1, 0);
+    sp.fw_f_off.assign(T_ + 1, 0); sp.fw_f_cnt.assign(T_ + 1, 0);
+    sp.bk_off.assign(T_ + 1, 0); sp.bk_cnt.assign(T_ + 1, 0);
+    auto mk = [](T* out, long long ldo, const T* cin, long long ldc, long long ldx, T alpha) {
+        SweepProb<T> p;
+        memset(&p, 0, sizeof(p));
+        p.out = out; p.ldo = ldo; p.cin = cin; p.ldc = ldc; p.ldx = ldx; p.alpha = alpha;
+        return p;
+    };
+    for (int t = 0; t <= T_; ++t) {
+        const Level& L = h->lev[t];
+        const long long ldF = (long long)L.m * b, ldG = (long long)L.ne * b;
+        const T* dinv = h->P<T>(L.off_dinv);
+        sp.fw_g_off[t] = pr.size();
+        for (int e = 0; e < L.ne; ++e) {
+            SweepProb<T> p = mk(Gp(t) + (size_t)e * b, ldG, nullptr, 0, ldF, T(1));
+            p.m[0] = dinv + e * bb;
+            p.x[0] = Fp(t) + (size_t)(2 * e) * b;
+            pr.push_back(p);
+        }
+        sp.fw_g_cnt[t] = pr.size() - sp.fw_g_off[t];
+        sp.fw_f_off[t] = pr.size();
+        if (t < T_) {
+            const T* ak = h->P<T>(L.off_ak);
+            const T* ck = h->P<T>(L.off_ck);
+            const long long ldN = (long long)L.nk * b;
+            for (int k = 0; k < L.nk; ++k) {
+                const int i = 2 * k + 1;
+                SweepProb<T> p = mk(Fp(t + 1) + (size_t)k * b, ldN, Fp(t) + (size_t)i * b, ldF, ldG, T(-1));
+                p.m[0] = ak + k * bb;
+                p.x[0] = Gp(t) + (size_t)k * b;
+                if (i + 1 < L.m) { p.m[1] = ck + k * bb; p.x[1] = Gp(t) + (size_t)(k + 1) * b; }
+                pr.push_back(p);
+            }
+        }
+        sp.fw_f_cnt[t] = pr.size() - sp.fw_f_off[t];
+    }
+    // back-substitution
+    for (int t = T_; t >= 0; --t) {
+        const Level& L = h->lev[t];
+        const long long ldF = (long long)L.m * b, ldG = (long long)L.ne * b;
+        sp.bk_off[t] = pr.size();
+        if (t == T_) {
+            pr.push_back(mk(Fp(t), ldF, Gp(t), ldG, 0, T(0)));
+        } else {
+            const T* xa = h->P<T>(L.off_xa);
+            const T* xc = h->P<T>(L.off_xc);
+            const long long ldU = (long long)L.nk * b;
+            T* Un = Fp(t + 1);
+            for (int i = 0; i < L.m; ++i) {
+                if (i & 1) {
+                    pr.push_back(mk(Fp(t) + (size_t)i * b, ldF, Un + (size_t)((i - 1) / 2) * b, ldU, 0, T(0)));
+                } else {
+                    const int e = i / 2;
+                    SweepProb<T> p = mk(Fp(t) + (size_t)i * b, ldF, Gp(t) + (size_t)e * b, ldG, ldU, T(-1));
+                    if (i > 0) { p.m[0] = xa + e * bb; p.x[0] = Un + (size_t)((i - 2) / 2) * b; }
+                    if (i + 1 < L.m) { p.m[1] = xc + e * bb; p.x[1] = Un + (size_t)(i / 2) * b; }
+                    pr.push_back(p);
+                }
+            }
+        }
+        sp.bk_cnt[t] = pr.size() - sp.bk_off[t];
+    }
+    CK(sp.dprobs.alloc(pr.size() * sizeof(SweepProb<T>), s));
+    CK(cudaMemcpyAsync(sp.dprobs.p, pr.data(), pr.size() * sizeof(SweepProb<T>), cudaMemcpyHostToDevice, s));
+    sp.nrhs = nrhs;
+    return ACR_OK;
+}
+
+template <class T>
+int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
+    const int b = h->b, T_ = h->levels() - 1, nrhs = sp.nrhs;
+    cudaStream_t s = h->stream;
+    const SweepProb<T>* dp = sp.dprobs.template as<SweepProb<T>>();
+    for (int t = 0; t <= T_; ++t) {
+        CK(sweep_batched<T>(dp + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], b, nrhs, s));
+        if (sp.fw_f_cnt[t]) CK(sweep_batched<T>(dp + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], b, nrhs, s));
+    }
+    for (int t = T_; t >= 0; --t) CK(sweep_batched<T>(dp + sp.bk_off[t], (int)sp.bk_cnt[t], b, nrhs, s));
+    return ACR_OK;
+}
+
+// r = f - M x with the FP64 operator copy.
+struct ResidPlan {
+    DevBuf dprobs;
+    int nprob = 0;
+};
+
+int build_resid_dense(acr_ctx* h, const double* x, const double* f, double* r, int nrhs, ResidPlan& rp) {
+    const int n = h->n, b = h->b;
+    const size_t bb = h->bb();
+    const double* oA = h->op.as<double>();
+    const double* oD = oA + (size_t)n * bb;
+    const double* oC = oD + (size_t)n * bb;
+    const long long N = (long long)n * b;
+    std::vector<SweepProb<double>> pr;
+    for (int i = 0; i < n; ++i) {
+        SweepProb<double> p;
+        memset(&p, 0, sizeof(p));
+        p.out = r + (size_t)i * b; p.ldo = N;
+        p.cin = f + (size_t)i * b; p.ldc = N;
+        p.ldx = N; p.alpha = -1.0;
+        p.m[0] = oD + i * bb; p.x[0] = x + (size_t)i * b;
+        if (i > 0) { p.m[1] = oA + i * bb; p.x[1] = x + (size_t)(i - 1) * b; }
+        if (i + 1 < n) { p.m[2] = oC + i * bb; p.x[2] = x + (size_t)(i + 1) * b; }
+        pr.push_back(p);
+    }
+    CK(rp.dprobs.alloc(pr.size() * sizeof(SweepProb<double>), h->stream));
+    CK(cudaMemcpyAsync(rp.dprobs.p, pr.data(), pr.size() * sizeof(SweepProb<double>), cudaMemcpyHostToDevice, h->stream));
+    rp.nprob = (int)pr.size();
+    return ACR_OK;
+}
+
+int residual(acr_ctx* h, const double* x, const double* f, double* r, int nrhs, ResidPlan* rp) {
+    const int n = h->n, b = h->b;
+    if (h->in_kind == ACR_BANDED) {
+        const size_t N = (size_t)n * b;
+        const double* o = h->op.as<double>();
+        CK(resid_banded(n, b, o, o + N, o + 2 * N, o + 3 * N, o + 4 * N, x, f, r, nrhs, h->stream));
+    } else {
+        CK(sweep_batched<double>(rp->dprobs.as<SweepProb<double>>(), rp->nprob, b, nrhs, h->stream));
+    }
+    return ACR_OK;
+}
+
+int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_out) {
+    const int n = h->n, b = h->b;
+    const long long N = (long long)n * b;
+    cudaStream_t s = h->stream;
+    const size_t bytes = (size_t)N * nrhs * 8;
+    const bool dev = is_device_ptr(B);
+    DevBuf dB;
+    double* f = B;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    if (!dev) {
+        CK(dB.alloc(bytes, s));
+        CK(cudaMemcpyAsync(dB.p, B, bytes, cudaMemcpyHostToDevice, s));
+        f = dB.as<double>();
+    }
+    CK(cudaEventRecord(e0, s));
+    int iters = 0;
+    int status = ACR_OK;
+    std::vector<double> rel(nrhs, 0.0);
+    const bool want_resid = resid_out != nullptr;
+    if (h->prec == ACR_FP64) {
+        // FP64 sweeps in place; keep f for the residual if asked for
+        DevBuf f0, r, ws, sq;
+        double* x = f;
+        if (want_resid) {
+            CK(f0.alloc(bytes, s));
+            CK(cudaMemcpyAsync(f0.p, f, bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        SweepPlan<double> sp;
+        int st = build_sweep<double>(h, x, nrhs, sp);
+        if (st) return st;
+        st = run_sweep<double>(h, sp);
+        if (st) return st;
+        if (want_resid) {
+            CK(r.alloc(bytes, s));
+            CK(ws.alloc((size_t)nrhs * 1024 * 8, s));
+            CK(sq.alloc((size_t)nrhs * 2 * 8, s));
+            ResidPlan rp;
+            if (h->in_kind != ACR_BANDED && (st = build_resid_dense(h, x, f0.as<double>(), r.as<double>(), nrhs, rp))) return st;
+            if ((st = residual(h, x, f0.as<double>(), r.as<double>(), nrhs, &rp))) return st;
+            CK(col_sumsq(r.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>(), s));
+            CK(col_sumsq(f0.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>() + nrhs, s));
+            std::vector<double> hs(2 * nrhs);
+            CK(cudaMemcpyAsync(hs.data(), sq.p, 2 * nrhs * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int q = 0; q < nrhs; ++q) rel[q] = hs[nrhs + q] > 0 ? std::sqrt(hs[q] / hs[nrhs + q]) : std::sqrt(hs[q]);
+        }
+    } else {
+        // mixed precision: FP32 sweeps, FP64 residual and correction
+        DevBuf x, r, f32, ws, sq;
+        CK(x.alloc(bytes, s));
+        CK(r.alloc(bytes, s));
+        CK(f32.alloc((size_t)N * nrhs * 4, s));
+        CK(ws.alloc((size_t)nrhs * 1024 * 8, s));
+        CK(sq.alloc((size_t)nrhs * 2 * 8, s));
+        CK(cudaMemsetAsync(x.p, 0, bytes, s));
+        CK(cudaMemcpyAsync(r.p, f, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(col_sumsq(f, N, nrhs, ws.as<double>(), sq.as<double>() + nrhs, s));
+        SweepPlan<float> sp;
+        int st = build_sweep<float>(h, f32.as<float>(), nrhs, sp);
+        if (st) return st;
+        ResidPlan rp;
+        if (h->in_kind != ACR_BANDED && (st = build_resid_dense(h, x.as<double>(), f, r.as<double>(), nrhs, rp))) return st;
+        std::vector<double> hs(2 * nrhs);
+        const int maxit = std::max(1, h->opts.ir_max_iter);
+        const double tol = h->opts.ir_tol;
+        bool conv = false;
+        for (iters = 1; iters <= maxit; ++iters) {
+            CK(convert_d2f(r.as<double>(), f32.as<float>(), (long long)N * nrhs, s));
+            if ((st = run_sweep<float>(h, sp))) return st;
+            CK(add_f2d(x.as<double>(), f32.as<float>(), (long long)N * nrhs, s));
+            if ((st = residual(h, x.as<double>(), f, r.as<double>(), nrhs, &rp))) return st;
+            CK(col_sumsq(r.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>(), s));
+            CK(cudaMemcpyAsync(hs.data(), sq.p, 2 * nrhs * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            conv = true;
+            for (int q = 0; q < nrhs; ++q) {
+                rel[q] = hs[nrhs + q] > 0 ? std::sqrt(hs[q] / hs[nrhs + q]) : std::sqrt(hs[q]);
+                if (!(rel[q] <= tol)) conv = false;
+            }
+            if (conv) break;
+        }
+        if (!conv) {
+            iters = maxit;
+            status = fail(ACR_ERR_NOT_CONVERGED, "refinement reached %d iterations without ||r||/||b|| <= %g", maxit, tol);
+        }
+        CK(cudaMemcpyAsync(f, x.p, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaEventRecord(e1, s));
+    if (!dev) CK(cudaMemcpyAsync(B, dB.p, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->st.solve_ms = ms;
+        h->st.ir_iters = h->prec == ACR_FP64 ? 0 : iters;
+        double mx = 0.0;
+        for (double v : rel) mx = std::max(mx, v);
+        h->st.ir_resid_max = mx;
+    }
+    if (resid_out) memcpy(resid_out, rel.data(), sizeof(double) * nrhs);
+    if (iters_out) *iters_out = h->prec == ACR_FP64 ? 0 : iters;
+    return status;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void acr_default_opts(acr_opts* o) {
+    if (o) default_opts(o);
+}
+
+const char* acr_last_error(void) { return g_err.c_str(); }
+
+int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts* o, size_t* bytes) {
+    (void)tol;
+    if (nblk < 1 || blksz < 1 || !bytes) return fail(ACR_ERR_INVALID_ARG, "bad arguments");
+    acr_opts op;
+    if (o) op = *o; else default_opts(&op);
+    const size_t es = op.precision == ACR_FP64 ? 8 : 4;
+    std::vector<Level> lev;
+    size_t arena = plan_levels(nblk, blksz, es, lev);
+    const size_t N = (size_t)nblk * blksz;
+    const size_t opb = op.input_kind == ACR_BANDED ? 5 * N * 8 : 3 * (size_t)nblk * blksz * blksz * 8;
+    *bytes = arena + opb;
+    return ACR_OK;
+}
+
+int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const double* C, double tol,
+                  const acr_opts* o, acr_handle* out) {
+    if (!out) return fail(ACR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nblk < 1 || blksz < 1) return fail(ACR_ERR_INVALID_ARG, "nblk and blksz must be >= 1 (got %d, %d)", nblk, blksz);
+    if (!D || (nblk > 1 && (!A || !C))) return fail(ACR_ERR_INVALID_ARG, "NULL block array");
+    if ((size_t)nblk * blksz > (size_t)1 << 31) return fail(ACR_ERR_INVALID_ARG, "system too large");
+    acr_opts op;
+    if (o) op = *o; else default_opts(&op);
+    if (op.precision < ACR_FP64 || op.precision > ACR_FP32_IR) return fail(ACR_ERR_INVALID_ARG, "unknown precision %d", op.precision);
+    if (op.input_kind != ACR_DENSE && op.input_kind != ACR_BANDED) return fail(ACR_ERR_INVALID_ARG, "unknown input_kind %d", op.input_kind);
+    if (op.m_stop > 1) return fail(ACR_ERR_INVALID_ARG, "m_stop > 1 is not supported (reduction runs to one block)");
+    if (op.ir_max_iter <= 0) op.ir_max_iter = 20;
+    if (!(op.ir_tol > 0)) op.ir_tol = 1e-8;
+    if (tol > 0) return fail(ACR_ERR_INVALID_ARG, "compressed (HODLR) blocks: tol > 0 not available in this build");
+    if (op.precision == ACR_FP32TC_IR) return fail(ACR_ERR_INVALID_ARG, "tensor-core products not available in this build");
+    acr_ctx* h = new (std::nothrow) acr_ctx();
+    if (!h) return fail(ACR_ERR_OOM, "host allocation failed");
+    h->n = nblk; h->b = blksz; h->prec = op.precision; h->in_kind = op.input_kind; h->tol = tol; h->opts = op;
+    cudaGetDevice(&h->dev);
+    if (op.stream) {
+        h->stream = static_cast<cudaStream_t>(op.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(ACR_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    h->es = op.precision == ACR_FP64 ? 8 : 4;
+    h->st.nblk = nblk; h->st.blksz = blksz; h->st.precision = op.precision; h->st.compressed = 0;
+    int st = (h->es == 8) ? run_factor<double>(h, A, D, C) : run_factor<float>(h, A, D, C);
+    if (st != ACR_OK) {
+        std::string msg = g_err;
+        cudaStreamSynchronize(h->stream);
+        delete h;
+        g_err = msg;
+        return st;
+    }
+    h->st.levels = h->levels();
+    *out = h;
+    return ACR_OK;
+}
+
+int acr_factor(int nblk, int blksz, const double* A, const double* D, const double* C, double tol, acr_handle* out) {
+    return acr_factor_ex(nblk, blksz, A, D, C, tol, nullptr, out);
+}
+
+int acr_solve_ex(acr_handle h, double* B, int nrhs, double* resid_out, int* iters_out) {
+    if (!h) return fail(ACR_ERR_INVALID_ARG, "NULL handle");
+    if (nrhs < 0 || (nrhs > 0 && !B)) return fail(ACR_ERR_INVALID_ARG, "bad right-hand side");
+    if (iters_out) *iters_out = 0;
+    if (nrhs == 0) return ACR_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != h->dev) cudaSetDevice(h->dev);
+    int st = solve_impl(h, B, nrhs, resid_out, iters_out);
+    if (prev != h->dev) cudaSetDevice(prev);
+    return st;
+}
+
+int acr_solve(acr_handle h, double* B, int nrhs) { return acr_solve_ex(h, B, nrhs, nullptr, nullptr); }
+
+void acr_free(acr_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+int acr_stats(acr_handle h, acr_stats_t* s) {
+    if (!h || !s) return fail(ACR_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(h->mu);
+    *s = h->st;
+    return ACR_OK;
+}
+
+}  // extern "C"

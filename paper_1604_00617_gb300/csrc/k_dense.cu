@@ -1,0 +1,742 @@
+// k_dense.cu -- dense block kernels of the block cyclic reduction path.
+//
+//  * batched Gauss-Jordan inversion with partial pivoting: the block-diagonal
+//    H11 of the even/odd permuted system is inverted block by block
+//    (Section 3, "its inverse can be computed as the inverse of each
+//    individual block");
+//  * batched multi-term block products for D_j^-1 A_j, D_j^-1 C_j and the
+//    Schur complement H22 - H21 H11^-1 H12 (Section 3, Eq. "fund");
+//  * batched block x multi-vector products for the right-hand-side reduction
+//    f^(1) = f_odd - H21 H11^-1 f_even and the back-substitution;
+//  * FP64 refinement helpers (residual with the original 5-point operator,
+//    column norms, conversions).
+//
+// All blocks are column-major with leading dimension b.
+#include <cfloat>
+#include <cmath>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+template <class T> struct Lim;
+template <> struct Lim<float> { static __device__ __forceinline__ float eps() { return FLT_EPSILON; } };
+template <> struct Lim<double> { static __device__ __forceinline__ double eps() { return DBL_EPSILON; } };
+
+template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+template <class T> __device__ __forceinline__ bool tfinite(T x) { return isfinite(x); }
+
+// Block-wide reduction helpers (blockDim.x multiple of 32, <= 1024).
+template <class T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = (l < nw) ? red[l] : T(0);
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;  // valid in every thread
+}
+
+// Arg-max of |value| with the lowest index winning ties.  Every thread passes
+// its candidate (val >= 0, idx; idx = INT_MAX for none).  Returns in all threads.
+template <class T>
+__device__ __forceinline__ void block_argmax(T& val, int& idx, T* rv, int* ri) {
+    for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, val, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) { rv[w] = val; ri[w] = idx; }
+    __syncthreads();
+    if (l < nw) { val = rv[l]; idx = ri[l]; } else { val = T(-1); idx = 0x7fffffff; }
+    for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, val, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+}
+
+// ===========================================================================
+// Gauss-Jordan inversion, one CTA per block, whole block in shared memory.
+// In-place GJ with row interchanges; the inverse is unscrambled by applying
+// the column interchanges in reverse order.  Singular test: a pivot that is
+// not finite or |p| <= 16 eps max|D| records info = k+1 (the factor still
+// runs to completion on a pivot of 1 so that nothing downstream faults).
+// ===========================================================================
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_gj_small(T* __restrict__ mats, int b, int* __restrict__ info) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = b + 1;
+    T* M = reinterpret_cast<T*>(smem_raw);
+    int* piv = reinterpret_cast<int*>(M + (size_t)ld * b);
+    int* csrc = piv + b;
+    __shared__ T rv[32];
+    __shared__ int ri[32];
+    __shared__ int s_info;
+    T* G = mats + (size_t)blockIdx.x * b * b;
+    const int tid = threadIdx.x;
+
+    T amax = T(0);
+    bool fin = true;
+    for (int i = tid; i < b * b; i += NT) {
+        const int r = i % b, c = i / b;
+        const T v = G[i];
+        M[r + c * ld] = v;
+        fin &= tfinite(v);
+        amax = fmax(amax, tabs(v));
+    }
+    if (!fin) amax = T(INFINITY);
+    if (tid == 0) s_info = 0;
+    amax = block_max(amax, rv);
+    const T tiny = T(16) * Lim<T>::eps() * amax;
+
+    for (int k = 0; k < b; ++k) {
+        T val = T(-1);
+        int idx = 0x7fffffff;
+        for (int r = k + tid; r < b; r += NT) {
+            const T v = tabs(M[r + k * ld]);
+            if (v > val || (v == val && r < idx)) { val = v; idx = r; }
+        }
+        block_argmax(val, idx, rv, ri);
+        const int p = (idx < b) ? idx : k;
+        const bool bad = !(val > tiny) || !tfinite(val);
+        if (tid == 0) {
+            piv[k] = p;
+            if (bad && s_info == 0) s_info = k + 1;
+        }
+        if (p != k)
+            for (int c = tid; c < b; c += NT) {
+                const T t = M[k + c * ld];
+                M[k + c * ld] = M[p + c * ld];
+                M[p + c * ld] = t;
+            }
+        __syncthreads();
+        const T pv = M[k + k * ld];
+        const T inv = bad ? T(1) : T(1) / pv;
+        __syncthreads();
+        for (int c = tid; c < b; c += NT)
+            if (c != k) M[k + c * ld] *= inv;
+        __syncthreads();
+        for (int i = tid; i < b * b; i += NT) {
+            const int r = i % b, c = i / b;
+            if (r != k && c != k) M[r + c * ld] -= M[r + k * ld] * M[k + c * ld];
+        }
+        __syncthreads();
+        for (int r = tid; r < b; r += NT)
+            M[r + k * ld] = (r == k) ? inv : -M[r + k * ld] * inv;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        for (int c = 0; c < b; ++c) csrc[c] = c;
+        for (int k = b - 1; k >= 0; --k) {
+            const int p = piv[k];
+            const int t = csrc[k]; csrc[k] = csrc[p]; csrc[p] = t;
+        }
+        info[blockIdx.x] = s_info;
+    }
+    __syncthreads();
+    for (int i = tid; i < b * b; i += NT) {
+        const int r = i % b, c = i / b;
+        G[i] = M[r + csrc[c] * ld];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan for blocks too large for shared memory.  Panel step:
+// one CTA per block runs the GJ steps of pivots k0..k0+kb-1 on the b x kb
+// panel of columns [k0, k0+kb) held in shared memory, recording the row
+// interchanges.  Update step: every other column j gets
+//     M[:, j] <- (P M)[:, j] with rows K zeroed + Panel * (P M)[K, j]
+// (P: the panel's row interchanges), which is exactly the effect of the same
+// GJ steps on that column.
+// ---------------------------------------------------------------------------
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, int k0, int kb,
+                                                 int* __restrict__ pivs, int* __restrict__ info,
+                                                 const T* __restrict__ amax_in) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* P = reinterpret_cast<T*>(smem_raw);  // b x kb, leading dim b
+    __shared__ T rv[32];
+    __shared__ int ri[32];
+    T* G = mats + (size_t)blockIdx.x * b * b;
+    int* piv = pivs + (size_t)blockIdx.x * b;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < b * kb; i += NT) P[i] = G[(size_t)k0 * b + i];
+    const T tiny = T(16) * Lim<T>::eps() * amax_in[blockIdx.x];
+    int first_bad = 0;
+    __syncthreads();
+    for (int kk = 0; kk < kb; ++kk) {
+        const int k = k0 + kk;
+        T val = T(-1);
+        int idx = 0x7fffffff;
+        for (int r = k + tid; r < b; r += NT) {
+            const T v = tabs(P[r + kk * b]);
+            if (v > val || (v == val && r < idx)) { val = v; idx = r; }
+        }
+        block_argmax(val, idx, rv, ri);
+        const int p = (idx < b) ? idx : k;
+        const bool bad = !(val > tiny) || !tfinite(val);
+        if (bad && first_bad == 0) first_bad = k + 1;
+        if (tid == 0) piv[k] = p;
+        if (p != k)
+            for (int c = tid; c < kb; c += NT) {
+                const T t = P[k + c * b];
+                P[k + c * b] = P[p + c * b];
+                P[p + c * b] = t;
+            }
+        __syncthreads();
+        const T inv = bad ? T(1) : T(1) / P[k + kk * b];
+        __syncthreads();
+        for (int c = tid; c < kb; c += NT)
+            if (c != kk) P[k + c * b] *= inv;
+        __syncthreads();
+        for (int i = tid; i < b * kb; i += NT) {
+            const int r = i % b, c = i / b;
+            if (r != k && c != kk) P[r + c * b] -= P[r + kk * b] * P[k + c * b];
+        }
+        __syncthreads();
+        for (int r = tid; r < b; r += NT)
+            P[r + kk * b] = (r == k) ? inv : -P[r + kk * b] * inv;
+        __syncthreads();
+    }
+    for (int i = tid; i < b * kb; i += NT) G[(size_t)k0 * b + i] = P[i];
+    if (tid == 0 && first_bad && info[blockIdx.x] == 0) info[blockIdx.x] = first_bad;
+}
+
+template <class T, int NT, int JT>
+__global__ void __launch_bounds__(NT) k_gj_update(T* __restrict__ mats, int b, int k0, int kb,
+                                                  const int* __restrict__ pivs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // stash: (2*kb) x JT values of displaced rows; T rows (the panel's pivot
+    // rows after interchange) occupy slots [0, kb)
+    T* stash = reinterpret_cast<T*>(smem_raw);
+    int* perm = reinterpret_cast<int*>(stash + 2 * kb * JT);   // b
+    int* slot = perm + b;                                      // b
+    int* list = slot + b;                                      // kb
+    __shared__ int s_cnt;
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* piv = pivs + (size_t)blockIdx.y * b;
+    const int tid = threadIdx.x;
+    const int nJ = b - kb;
+    const int j0 = blockIdx.x * JT;
+    for (int r = tid; r < b; r += NT) { perm[r] = r; slot[r] = -1; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int kk = 0; kk < kb; ++kk) {
+            const int k = k0 + kk, p = piv[k];
+            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+            slot[k] = kk;
+        }
+        int cnt = 0;
+        for (int kk = 0; kk < kb; ++kk) {
+            const int p = piv[k0 + kk];
+            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
+        }
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    const int ns = kb + s_cnt;
+    for (int i = tid; i < ns * JT; i += NT) {
+        const int s = i % ns, j = i / ns;
+        const int jc = j0 + j;
+        T v = T(0);
+        if (jc < nJ) {
+            const int c = jc < k0 ? jc : jc + kb;
+            const int r = s < kb ? k0 + s : list[s - kb];
+            v = G[perm[r] + (size_t)c * b];
+        }
+        stash[s + j * 2 * kb] = v;
+    }
+    __syncthreads();
+    int ncol = nJ - j0;
+    if (ncol > JT) ncol = JT;
+    for (int r = tid; r < b; r += NT) {
+        T acc[JT];
+        const int sl = slot[r];
+#pragma unroll
+        for (int j = 0; j < JT; ++j) {
+            const int jc = j0 + j;
+            const int c = jc < k0 ? jc : jc + kb;
+            T base = T(0);
+            if (j < ncol) base = (sl < 0) ? G[r + (size_t)c * b] : (sl < kb ? T(0) : stash[sl + j * 2 * kb]);
+            acc[j] = base;
+        }
+        for (int kk = 0; kk < kb; ++kk) {
+            const T pv = G[r + (size_t)(k0 + kk) * b];
+#pragma unroll
+            for (int j = 0; j < JT; ++j) acc[j] += pv * stash[kk + j * 2 * kb];
+        }
+#pragma unroll
+        for (int j = 0; j < JT; ++j) {
+            if (j < ncol) {
+                const int jc = j0 + j;
+                const int c = jc < k0 ? jc : jc + kb;
+                G[r + (size_t)c * b] = acc[j];
+            }
+        }
+    }
+}
+
+// Column interchanges in reverse order, one thread per row.
+template <class T>
+__global__ void k_gj_unscramble(T* __restrict__ mats, int b, const int* __restrict__ pivs) {
+    extern __shared__ int spiv[];
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* piv = pivs + (size_t)blockIdx.y * b;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) spiv[i] = piv[i];
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= b) return;
+    for (int k = b - 1; k >= 0; --k) {
+        const int p = spiv[k];
+        if (p != k) {
+            const T t = G[r + (size_t)k * b];
+            G[r + (size_t)k * b] = G[r + (size_t)p * b];
+            G[r + (size_t)p * b] = t;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_maxabs(const T* __restrict__ mats, int b, T* __restrict__ out) {
+    __shared__ T red[32];
+    const T* G = mats + (size_t)blockIdx.x * b * b;
+    T m = T(0);
+    bool fin = true;
+    for (size_t i = threadIdx.x; i < (size_t)b * b; i += blockDim.x) {
+        const T v = G[i];
+        fin &= tfinite(v);
+        m = fmax(m, tabs(v));
+    }
+    if (!fin) m = T(INFINITY);
+    m = block_max(m, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = m;
+}
+
+template <class T>
+static size_t gj_small_smem(int b) {
+    return (size_t)(b + 1) * b * sizeof(T) + 2 * (size_t)b * sizeof(int);
+}
+
+template <class T>
+cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    cudaMemsetAsync(info, 0, sizeof(int) * count, s);
+    const size_t small = gj_small_smem<T>(b);
+    if (small <= 200 * 1024) {
+        auto kern = k_gj_small<T, 256>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
+        kern<<<count, 256, small, s>>>(mats, b, info);
+        return cudaGetLastError();
+    }
+    // blocked path
+    const int kb = sizeof(T) == 8 ? 16 : 32;
+    T* amax = nullptr;
+    cudaError_t e = cudaMallocAsync(&amax, sizeof(T) * count, s);
+    if (e != cudaSuccess) return e;
+    k_maxabs<T><<<count, 256, 0, s>>>(mats, b, amax);
+    constexpr int JT = 16;
+    const size_t psmem = (size_t)b * kb * sizeof(T);
+    const size_t usmem = (size_t)2 * kb * JT * sizeof(T) + (2 * (size_t)b + kb) * sizeof(int);
+    auto kp = k_gj_panel<T, 512>;
+    auto ku = k_gj_update<T, 256, JT>;
+    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+    for (int k0 = 0; k0 < b; k0 += kb) {
+        const int kbi = (b - k0) < kb ? (b - k0) : kb;
+        kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
+        const int nJ = b - kbi;
+        if (nJ > 0) {
+            dim3 g((nJ + JT - 1) / JT, count);
+            ku<<<g, 256, usmem, s>>>(mats, b, k0, kbi, ws_piv);
+        }
+    }
+    dim3 gu((b + 255) / 256, count);
+    k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
+    cudaFreeAsync(amax, s);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Batched multi-term block product on CUDA cores (SIMT).
+// CTA tile BM x BN, K step BK, thread tile TM x TN (rows interleaved so that
+// consecutive lanes store consecutive rows).
+// ===========================================================================
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm_simt(const GemmProb<T>* __restrict__ probs, int b, int tiles_m) {
+    constexpr int RY = BM / TM, RX = BN / TN, NT = RY * RX;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN + 1];
+    const GemmProb<T> P = probs[blockIdx.y];
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int row0 = tm * BM, col0 = tn * BN;
+    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int t = 0; t < 2; ++t) {
+        const T* __restrict__ A = P.a[t];
+        const T* __restrict__ B = P.bm[t];
+        if (A == nullptr) continue;
+        for (int k0 = 0; k0 < b; k0 += BK) {
+#pragma unroll
+            for (int i = tid; i < BM * BK; i += NT) {
+                const int r = i % BM, k = i / BM;
+                const int gr = row0 + r, gk = k0 + k;
+                As[k][r] = (gr < b && gk < b) ? A[gr + (size_t)gk * b] : T(0);
+            }
+#pragma unroll
+            for (int i = tid; i < BK * BN; i += NT) {
+                const int k = i % BK, c = i / BK;
+                const int gk = k0 + k, gc = col0 + c;
+                Bs[k][c] = (gk < b && gc < b) ? B[gk + (size_t)gc * b] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T af[TM], bf[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) af[i] = As[kk][ty + i * RY];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) bf[j] = Bs[kk][tx + j * RX];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int c = col0 + tx + j * RX;
+        if (c >= b) continue;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + ty + i * RY;
+            if (r >= b) continue;
+            const size_t o = r + (size_t)c * b;
+            T v = P.alpha * acc[i][j];
+            if (P.cin) v += P.beta * P.cin[o];
+            P.out[o] = v;
+        }
+    }
+}
+
+template <class T>
+cudaError_t gemm_simt(const GemmProb<T>* d_probs, int nprob, int b, cudaStream_t s) {
+    if (nprob <= 0) return cudaSuccess;
+    if (sizeof(T) == 8) {
+        constexpr int BM = 64, BN = 64;
+        const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
+        dim3 g(tm * tn, nprob);
+        k_gemm_simt<T, BM, BN, 8, 4, 4><<<g, 256, 0, s>>>(d_probs, b, tm);
+    } else if (b >= 128) {
+        constexpr int BM = 128, BN = 128;
+        const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
+        dim3 g(tm * tn, nprob);
+        k_gemm_simt<T, BM, BN, 8, 8, 8><<<g, 256, 0, s>>>(d_probs, b, tm);
+    } else {
+        constexpr int BM = 64, BN = 64;
+        const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
+        dim3 g(tm * tn, nprob);
+        k_gemm_simt<T, BM, BN, 8, 4, 4><<<g, 256, 0, s>>>(d_probs, b, tm);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t gemm_batched(const GemmProb<T>* d_probs, int nprob, int b, int use_tc, cudaStream_t s) {
+    (void)use_tc;
+    return gemm_simt<T>(d_probs, nprob, b, s);
+}
+
+// ===========================================================================
+// Batched block x multi-vector products (solve sweeps).  One CTA computes RT
+// rows of one problem for NR right-hand sides at a time; KG thread groups
+// split the columns of the block, reduced through shared memory.
+// ===========================================================================
+template <class T, int NR, int RT, int KG, int KC>
+__global__ void __launch_bounds__(RT * KG)
+k_sweep(const SweepProb<T>* __restrict__ probs, int b, int nrhs, int row_tiles) {
+    constexpr int NT = RT * KG;
+    __shared__ T xs[KC][NR];
+    __shared__ T red[KG][RT][NR + 1];
+    const SweepProb<T> P = probs[blockIdx.y];
+    const int row0 = blockIdx.x * RT;
+    const int tid = threadIdx.x, lr = tid % RT, g = tid / RT;
+    const int row = row0 + lr;
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = (nrhs - q0) < NR ? (nrhs - q0) : NR;
+        T acc[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = T(0);
+        for (int t = 0; t < 3; ++t) {
+            const T* __restrict__ Mt = P.m[t];
+            if (Mt == nullptr) continue;
+            const T* __restrict__ X = P.x[t];
+            if ((P.diag_mask >> t) & 1) {
+                if (g == 0 && row < b) {
+                    const T d = Mt[row];
+#pragma unroll
+                    for (int q = 0; q < NR; ++q)
+                        if (q < nq) acc[q] += d * X[row + (size_t)(q0 + q) * P.ldx];
+                }
+                continue;
+            }
+            for (int kc = 0; kc < b; kc += KC) {
+                __syncthreads();
+                for (int i = tid; i < KC * NR; i += NT) {
+                    const int c = i % KC, q = i / KC;
+                    xs[c][q] = (kc + c < b && q < nq) ? X[kc + c + (size_t)(q0 + q) * P.ldx] : T(0);
+                }
+                __syncthreads();
+                if (row < b) {
+                    const int cend = (b - kc) < KC ? (b - kc) : KC;
+                    for (int c = g; c < cend; c += KG) {
+                        const T mv = Mt[row + (size_t)(kc + c) * b];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = fma(mv, xs[c][q], acc[q]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) red[g][lr][q] = acc[q];
+        __syncthreads();
+        for (int i = tid; i < RT * NR; i += NT) {
+            const int r = i % RT, q = i / RT;
+            const int gr = row0 + r;
+            if (gr < b && q < nq) {
+                T v = T(0);
+#pragma unroll
+                for (int gg = 0; gg < KG; ++gg) v += red[gg][r][q];
+                T o = P.alpha * v;
+                if (P.cin) o += P.cin[gr + (size_t)(q0 + q) * P.ldc];
+                P.out[gr + (size_t)(q0 + q) * P.ldo] = o;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+cudaError_t sweep_batched(const SweepProb<T>* d_probs, int nprob, int b, int nrhs, cudaStream_t s) {
+    if (nprob <= 0 || nrhs <= 0) return cudaSuccess;
+    constexpr int RT = 64, KG = 4, KC = 64;
+    dim3 g((b + RT - 1) / RT, nprob);
+    const int rt = g.x;
+    if (nrhs == 1)
+        k_sweep<T, 1, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+    else if (nrhs <= 4)
+        k_sweep<T, 4, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+    else if (nrhs <= 8)
+        k_sweep<T, 8, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+    else
+        k_sweep<T, 16, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Level-0 staging.
+// ===========================================================================
+template <class T>
+__global__ void k_stage_dense(int n, int b, const double* __restrict__ A, const double* __restrict__ D,
+                              const double* __restrict__ C, T* dinv, T* dodd, T* aev, T* ak, T* cev,
+                              T* ck, int* bad) {
+    const int j = blockIdx.y;  // block index
+    const size_t bb = (size_t)b * b;
+    const int slot = j >> 1;
+    T* dD = (j & 1) ? dodd + slot * bb : dinv + slot * bb;
+    T* dA = (j & 1) ? ak + slot * bb : aev + slot * bb;
+    T* dC = (j & 1) ? ck + slot * bb : cev + slot * bb;
+    const bool hasA = j > 0, hasC = j + 1 < n;
+    bool fin = true;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bb; i += (size_t)gridDim.x * blockDim.x) {
+        const double d = D[j * bb + i];
+        fin &= isfinite(d);
+        dD[i] = (T)d;
+        if (hasA) { const double v = A[j * bb + i]; fin &= isfinite(v); dA[i] = (T)v; }
+        if (hasC) { const double v = C[j * bb + i]; fin &= isfinite(v); dC[i] = (T)v; }
+    }
+    if (!fin) atomicExch(bad, 1);
+}
+
+template <class T>
+__global__ void k_stage_banded(int n, int b, const double* __restrict__ A, const double* __restrict__ D,
+                               const double* __restrict__ C, T* dinv, T* dodd, T* aev, T* ak, T* cev,
+                               T* ck, int* bad) {
+    const int j = blockIdx.y;
+    const size_t bb = (size_t)b * b;
+    const int slot = j >> 1;
+    T* dD = (j & 1) ? dodd + slot * bb : dinv + slot * bb;
+    T* dA = (j & 1) ? ak + slot * bb : aev + slot * bb;
+    T* dC = (j & 1) ? ck + slot * bb : cev + slot * bb;
+    const bool hasA = j > 0, hasC = j + 1 < n;
+    const double* Dl = D + (size_t)j * 3 * b;
+    const double* Dd = Dl + b;
+    const double* Du = Dd + b;
+    bool fin = true;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bb; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i % b), c = (int)(i / b);
+        double dv = 0.0;
+        if (r == c) dv = Dd[r];
+        else if (r == c + 1) dv = Dl[r];
+        else if (c == r + 1) dv = Du[r];
+        fin &= isfinite(dv);
+        dD[i] = (T)dv;
+        if (hasA) { const double v = (r == c) ? A[(size_t)j * b + r] : 0.0; fin &= isfinite(v); dA[i] = (T)v; }
+        if (hasC) { const double v = (r == c) ? C[(size_t)j * b + r] : 0.0; fin &= isfinite(v); dC[i] = (T)v; }
+    }
+    if (!fin) atomicExch(bad, 1);
+}
+
+template <class T>
+cudaError_t stage_level0(int in_kind, int n, int b, const double* A, const double* D, const double* C,
+                         T* dinv, T* dodd, T* aev, T* ak, T* cev, T* ck, int* bad, cudaStream_t s) {
+    const size_t bb = (size_t)b * b;
+    int gx = (int)((bb + 255) / 256);
+    if (gx > 64) gx = 64;
+    dim3 g(gx, n);
+    if (in_kind == 0)
+        k_stage_dense<T><<<g, 256, 0, s>>>(n, b, A, D, C, dinv, dodd, aev, ak, cev, ck, bad);
+    else
+        k_stage_banded<T><<<g, 256, 0, s>>>(n, b, A, D, C, dinv, dodd, aev, ak, cev, ck, bad);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// FP64 refinement helpers.
+// ===========================================================================
+__global__ void k_resid_banded(int n, int b, const double* __restrict__ Dl, const double* __restrict__ Dd,
+                               const double* __restrict__ Du, const double* __restrict__ a,
+                               const double* __restrict__ c, const double* __restrict__ x,
+                               const double* __restrict__ f, double* __restrict__ r, int nrhs) {
+    const long long N = (long long)n * b;
+    const long long total = N * nrhs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long g = t % N, q = t / N;
+        const int i = (int)(g / b), p = (int)(g % b);
+        const double* xq = x + q * N;
+        double y = Dd[g] * xq[g];
+        if (p > 0) y += Dl[(size_t)i * b + p] * xq[g - 1];
+        if (p + 1 < b) y += Du[(size_t)i * b + p] * xq[g + 1];
+        if (i > 0) y += a[g] * xq[g - b];
+        if (i + 1 < n) y += c[g] * xq[g + b];
+        r[t] = f[t] - y;
+    }
+}
+
+cudaError_t resid_banded(int n, int b, const double* Dl, const double* Dd, const double* Du,
+                         const double* a, const double* c, const double* x, const double* f, double* r,
+                         int nrhs, cudaStream_t s) {
+    const long long total = (long long)n * b * nrhs;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_resid_banded<<<(int)blocks, 256, 0, s>>>(n, b, Dl, Dd, Du, a, c, x, f, r, nrhs);
+    return cudaGetLastError();
+}
+
+__global__ void k_sumsq_partial(const double* __restrict__ v, long long N, double* __restrict__ ws) {
+    // grid (1024 chunks, nrhs)
+    __shared__ double red[32];
+    const int q = blockIdx.y;
+    const long long chunk = (N + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * chunk;
+    long long hi = lo + chunk;
+    if (hi > N) hi = N;
+    double s = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double t = v[i + q * N];
+        s += t * t;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) ws[q * (long long)gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sumsq_final(const double* __restrict__ ws, int chunks, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int q = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) s += ws[q * (long long)chunks + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) out[q] = s;
+    }
+}
+
+cudaError_t col_sumsq(const double* v, long long N, int nrhs, double* ws, double* sumsq, cudaStream_t s) {
+    if (nrhs <= 0) return cudaSuccess;
+    int chunks = 1024;
+    if (N < 1024 * 256) chunks = (int)((N + 255) / 256);
+    if (chunks < 1) chunks = 1;
+    k_sumsq_partial<<<dim3(chunks, nrhs), 256, 0, s>>>(v, N, ws);
+    k_sumsq_final<<<nrhs, 256, 0, s>>>(ws, chunks, sumsq);
+    return cudaGetLastError();
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void k_add_f2d(double* __restrict__ x, const float* __restrict__ d, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+__global__ void k_add_d2d(double* __restrict__ x, const double* __restrict__ d, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+static int ew_blocks(long long n) {
+    long long bl = (n + 255) / 256;
+    if (bl > 152 * 16) bl = 152 * 16;
+    return bl < 1 ? 1 : (int)bl;
+}
+cudaError_t convert_d2f(const double* src, float* dst, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_d2f<<<ew_blocks(n), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+cudaError_t add_f2d(double* x, const float* d, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_add_f2d<<<ew_blocks(n), 256, 0, s>>>(x, d, n);
+    return cudaGetLastError();
+}
+cudaError_t add_d2d(double* x, const double* d, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_add_d2d<<<ew_blocks(n), 256, 0, s>>>(x, d, n);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t gj_inverse<float>(float*, int, int, int*, int*, cudaStream_t);
+template cudaError_t gj_inverse<double>(double*, int, int, int*, int*, cudaStream_t);
+template cudaError_t gemm_batched<float>(const GemmProb<float>*, int, int, int, cudaStream_t);
+template cudaError_t gemm_batched<double>(const GemmProb<double>*, int, int, int, cudaStream_t);
+template cudaError_t sweep_batched<float>(const SweepProb<float>*, int, int, int, cudaStream_t);
+template cudaError_t sweep_batched<double>(const SweepProb<double>*, int, int, int, cudaStream_t);
+template cudaError_t stage_level0<float>(int, int, int, const double*, const double*, const double*, float*,
+                                         float*, float*, float*, float*, float*, int*, cudaStream_t);
+template cudaError_t stage_level0<double>(int, int, int, const double*, const double*, const double*, double*,
+                                          double*, double*, double*, double*, double*, int*, cudaStream_t);
+
+}  // namespace acr
