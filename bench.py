@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark of the block cyclic reduction hot path on one or more GPUs.
+
+Workload (default): the 2D indefinite Helmholtz problem on a 1024 x 1024 grid
+(N = 1,048,576; 1024 blocks of 1024 x 1024), 8 seeded uniform[-1, 1] right-hand
+sides, factor in FP32 (block products on tensor cores when built with them)
+and FP64 FGMRES refinement to a relative residual of 1e-8 per column.  One
+step = factor + solve of the 8 right-hand sides (every row of the hot path).
+
+``value`` = right-hand sides brought to 1e-8 per second, whole job (factor
+time included), inputs resident in HBM.  Multi-GPU runs are replicas (one
+independent system per rank, weak scaling).  ``--impl reference`` times the
+CPU oracle (dense FP64 block cyclic reduction) on a bounded sample of the
+same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ACR factor s & solves/s at N=1M (FP32-TC+IR vs FP64) @1e-8 resid; p50/p99 ms"
+UNIT = "solves/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=1024, help="grid size (blocks = blksz = n)")
+    p.add_argument("--nrhs", type=int, default=8)
+    p.add_argument("--prec", default="auto", choices=["auto", "fp32tc", "fp32", "fp64"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-blocks", type=int, default=32, help="oracle sample: leading grid lines")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n, nrhs):
+    import synthetic as syn
+    P = syn.helmholtz(n, seed=1003)
+    F = syn.rhs_uniform(P.N, nrhs, 2003)
+    return P, F
+
+
+def dense_bcr_flops(nblk, b):
+    """Algorithmic flops of dense block cyclic reduction (all blocks dense):
+    2 b^3 per block inverse and per block product."""
+    b3 = float(b) ** 3
+    f, m = 0.0, nblk
+    while True:
+        ne, nk = (m + 1) // 2, m // 2
+        f += 2 * b3 * ne
+        if m == 1:
+            break
+        f += 2 * b3 * (sum(1 for e in range(ne) if 2 * e > 0) + sum(1 for e in range(ne) if 2 * e + 1 < m))
+        for k in range(nk):
+            i = 2 * k + 1
+            f += 2 * b3 * (1 + (i + 1 < m) + (i >= 3) + (i + 2 < m))
+        m = nk
+    return f
+
+
+# ----------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.dev_id = dev_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.dev_id is not None:
+            cmd += ["-i", str(self.dev_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        busy = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one
+    exists for the current build of that kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    return rec
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline(P, nrhs, nblocks):
+    """The oracle (dense FP64 BCR, as it stands) on the leading `nblocks` grid
+    lines of the workload; its flop rate scaled to the full factor + solve."""
+    import oracle
+    import synthetic as syn
+    sub = syn.BlockTridiag(nblocks, P.b, P.Dl[:nblocks].copy(), P.Dd[:nblocks].copy(),
+                           P.Du[:nblocks].copy(), P.a[:nblocks].copy(), P.c[:nblocks].copy())
+    sub.c[-1] = 0.0
+    A, D, C = sub.dense_blocks()
+    F = syn.rhs_uniform(sub.N, nrhs, 2003)
+    t0 = time.perf_counter()
+    oracle.bcr_solve(A, D, C, F)
+    dt = time.perf_counter() - t0
+    f_sample = dense_bcr_flops(nblocks, P.b)
+    f_full = dense_bcr_flops(P.nblk, P.b)
+    est = dt * f_full / f_sample
+    return {"value": nrhs / est, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"dense FP64 BCR factor+solve of the first {nblocks} grid lines "
+                       f"({nblocks} blocks of {P.b}x{P.b}, {nrhs} RHS) of the same operator, "
+                       f"{dt:.2f} s; flop rate scaled to the full {P.nblk}-block factor "
+                       f"({f_full / 1e12:.1f} TFLOP): est. {est:.0f} s per step"),
+            "sample_s": dt, "est_step_s": est}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    P, _ = workload(args.n, args.nrhs)
+    nb = min(16, P.nblk)
+    times = []
+    for it in range(args.warmup + args.steps):
+        r = cpu_baseline(P, args.nrhs, nb)
+        if it >= args.warmup:
+            times.append(r)
+    est = statistics.median([t["est_step_s"] for t in times])
+    value = args.nrhs / est
+    cb = dict(times[-1])
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"helmholtz{args.n}", "nblk": P.nblk, "blksz": P.b, "nrhs": args.nrhs},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1604_00617_gb300 import build
+    if rank == 0 or ws == 1:
+        build()
+    if ws > 1:
+        torch.distributed.barrier()
+        build()
+    from paper_1604_00617_gb300 import _lib as acr
+
+    P, F = workload(args.n, args.nrhs)
+    a, D3, c = P.banded_abi()
+    N, nrhs = P.N, args.nrhs
+    stream = torch.cuda.current_stream()
+    da, dD3, dc = (torch.from_numpy(x).to(dev) for x in (a, D3, c))
+    dF = torch.from_numpy(np.ascontiguousarray(F.T)).to(dev)  # column-major N x nrhs
+    dB = torch.empty_like(dF)
+
+    prec = args.prec
+    tc_ok = os.environ.get("ACR_NO_TC") is None and hasattr(acr, "ACR_FP32TC_IR") and _tc_available(acr)
+    if prec == "auto":
+        prec = "fp32tc" if tc_ok else "fp32"
+    pmap = {"fp32tc": acr.ACR_FP32TC_IR, "fp32": acr.ACR_FP32_IR, "fp64": acr.ACR_FP64}
+
+    def opts(p):
+        o = acr.acr_default_opts()
+        o.precision = pmap[p]
+        o.input_kind = acr.ACR_BANDED
+        o.ir_tol = 1e-8
+        o.ir_max_iter = 60
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        return o
+
+    o = opts(prec)
+    stats = []
+
+    def step():
+        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, 0.0, o)
+        try:
+            dB.copy_(dF)
+            res, it = acr.acr_solve_ex(h, dB, nrhs)
+            s = acr.acr_stats(h)
+        finally:
+            acr.acr_free(h)
+        s["resid"] = res.tolist()
+        s["iters"] = it
+        return s
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = Clocks(_smi_id(dev))
+    clk.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        stats.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    # the library's calls are host-synchronous: device time between the events
+    # includes the host gaps between launches, so take the larger of the two
+    elapsed = max(dev_ms / 1e3, wall)
+    if ws > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = nrhs * args.steps * ws / elapsed
+
+    last = stats[-1]
+    kernel = "gemm_tc" if prec == "fp32tc" else ("gemm_simt_f32" if prec == "fp32" else "gemm_simt_f64")
+    peaks = measured_peaks()
+    gemm_tflops = statistics.median(s["gemm_flops"] / (s["gemm_ms"] * 1e-3) / 1e12 for s in stats)
+    sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    if prec == "fp32tc":
+        if peaks:
+            peak, src = peaks["bf16_tflops_sustained"] / 2.0, "of measured (bf16 sustained x 1/2, tf32 nominal ratio)"
+        else:
+            peak, src = 1700.0 / 2.0, "of fallback"
+        bound = "tensor"
+    elif prec == "fp32":
+        peak, src = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"
+        bound = "alu"
+    else:
+        peak, src = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 2 FP64 FMA/clk x 2 x max SM clock"
+        bound = "alu"
+    tr = traffic_record(kernel)
+    roof = {"kernel": kernel, "bound": bound, "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": gemm_tflops / peak, "peak_source": src,
+            "traffic": tr.get("bytes_per_launch") if tr else None,
+            "algorithmic_per_launch": last["gemm_flops"] / max(1, last["gemm_launches"]),
+            "launch_ms": last["gemm_ms"] / max(1, last["gemm_launches"])}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32tc": "f32(tf32x3 tc)+f64", "fp32": "f32+f64", "fp64": "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": f"helmholtz{args.n}: 2D Helmholtz -Lap u - kappa^2 u, {args.n}x{args.n} grid, "
+                                   f"N={N}, {P.nblk} blocks of {P.b}x{P.b}, {nrhs} RHS, 16 points per wavelength "
+                                   "+-20% seeded kappa, refinement to 1e-8",
+                       "nblk": P.nblk, "blksz": P.b, "nrhs": nrhs, "precision": prec,
+                       "l2": "inputs larger than L2 (factor storage %.1f GB vs 129 MB L2)" % (last["factor_bytes"] / 1e9),
+                       "parallelism": f"replicas x{ws}"},
+            "factor_s": statistics.median(s["factor_ms"] for s in stats) / 1e3,
+            "solve_s": statistics.median(s["solve_ms"] for s in stats) / 1e3,
+            "solves_per_s_resident": nrhs / (statistics.median(s["solve_ms"] for s in stats) / 1e3),
+            "iters": last["iters"], "resid_max": max(last["resid"]),
+            "kernels": {"gemm_ms": last["gemm_ms"], "gemm_tflops": last["gemm_flops"] / last["gemm_ms"] / 1e9,
+                        "inv_ms": last["inv_ms"], "inv_tflops": last["inv_flops"] / max(last["inv_ms"], 1e-9) / 1e9,
+                        "sweep_ms": last["sweep_ms"],
+                        "sweep_gbs": last["sweep_bytes"] / max(last["sweep_ms"], 1e-9) / 1e6},
+            "roofline": roof, "clocks": clocks,
+            "gpu_launches": int(sum(s["launches_factor"] + s["launches_solve"] for s in stats))}
+
+    # ---- FP64 comparator (same code, ACR_FP64), measured once ---------------
+    if not args.no_fp64 and prec != "fp64":
+        o64 = opts("fp64")
+        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, 0.0, o64)
+        try:
+            dB.copy_(dF)
+            try:
+                res, it = acr.acr_solve_ex(h, dB, nrhs)
+                conv = True
+            except acr.AcrError as e:
+                res, it, conv = e.resid, e.iters, False
+            s = acr.acr_stats(h)
+        finally:
+            acr.acr_free(h)
+        line["fp64"] = {"factor_s": s["factor_ms"] / 1e3, "solve_s": s["solve_ms"] / 1e3,
+                        "iters": it, "resid_max": float(np.max(res)), "converged": conv,
+                        "time_to_1e8_s": (s["factor_ms"] + s["solve_ms"]) / 1e3,
+                        "gemm_tflops": s["gemm_flops"] / s["gemm_ms"] / 1e9}
+        line["time_to_1e8_s"] = (line["factor_s"] + line["solve_s"])
+
+    # ---- end to end through the public API with host (pinned) buffers -----
+    if not args.no_e2e:
+        ha, hD3, hc = (torch.from_numpy(x).pin_memory() for x in (a, D3, c))
+        hF = torch.from_numpy(np.ascontiguousarray(F.T)).pin_memory()
+        hB = torch.empty_like(hF).pin_memory()
+        oe = opts(prec)
+        e_t = []
+        for k in range(1 + args.steps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            h = acr.acr_factor_ex(P.nblk, P.b, ha, hD3, hc, 0.0, oe)
+            hB.copy_(hF)
+            acr.acr_solve_ex(h, hB, nrhs)
+            acr.acr_free(h)
+            e_t.append(time.perf_counter() - t1)
+        et = statistics.median(e_t[1:])
+        line["e2e"] = {"value": nrhs * ws / et, "unit": UNIT,
+                       "h2d_bytes_per_step": int(a.nbytes + D3.nbytes + c.nbytes + F.nbytes),
+                       "d2h_bytes_per_step": int(F.nbytes), "s_per_step": et}
+
+    if rank == 0 and not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(P, nrhs, min(args.cpu_blocks, P.nblk))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def _tc_available(acr):
+    return getattr(acr, "TC_BUILT", True)
+
+
+def _smi_id(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -85,9 +85,22 @@ typedef struct {
     int m_stop;         /* stop the reduction at this many blocks; 1 only */
     double ir_tol;      /* refinement target ||f - M x||_2 / ||f||_2 per column
                            (default 1e-8) */
-    int ir_max_iter;    /* refinement iteration cap (default 20) */
+    int ir_max_iter;    /* cap on preconditioner solves per acr_solve (default 20) */
     void *stream;       /* cudaStream_t to run on; NULL: a library stream */
+    int refine;         /* enum acr_refine, default ACR_REFINE_FGMRES */
 } acr_opts;
+
+enum acr_refine {
+    /* restarted FGMRES(30) in FP64, right-preconditioned by the factor's
+     * sweeps (converges where plain refinement diverges, e.g. indefinite
+     * Helmholtz, whose reduced blocks amplify rounding errors) */
+    ACR_REFINE_FGMRES = 0,
+    /* classic iterative refinement x += M^-1 (f - A x) */
+    ACR_REFINE_IR = 1,
+    /* no refinement: one sweep (ACR_ERR_NOT_CONVERGED if the residual misses
+     * ir_tol) */
+    ACR_REFINE_NONE = 2
+};
 
 /* Fill *o with the defaults listed above. */
 void acr_default_opts(acr_opts *o);
@@ -131,6 +144,14 @@ typedef struct {
     double ir_resid_max;     /* max relative residual over columns, last solve */
     int rank_max[32];        /* HODLR: max off-diagonal rank per level */
     double rank_mean[32];    /* HODLR: mean off-diagonal rank per level */
+    /* per kernel class, last factor / last solve: device time (CUDA events
+     * on the library stream), algorithmic work, launches */
+    double gemm_ms, gemm_flops;          /* block products (factor) */
+    double inv_ms, inv_flops;            /* block inversions (factor) */
+    double sweep_ms, sweep_bytes;        /* solve sweeps, all passes */
+    long long gemm_launches, inv_launches, sweep_launches;
+    long long launches_factor;           /* all kernel launches, last factor */
+    long long launches_solve;            /* all kernel launches, last solve */
 } acr_stats_t;
 
 /* Copy the handle's statistics into *s. */

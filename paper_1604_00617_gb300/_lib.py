@@ -32,6 +32,13 @@ ACR_FP32_IR = 2
 ACR_DENSE = 0
 ACR_BANDED = 1
 
+# tensor-core block products compiled into this build
+TC_BUILT = False
+
+ACR_REFINE_FGMRES = 0
+ACR_REFINE_IR = 1
+ACR_REFINE_NONE = 2
+
 _NAMES = {0: "ACR_OK", -1: "ACR_ERR_INVALID_ARG", -2: "ACR_ERR_OOM", -3: "ACR_ERR_SINGULAR",
           -4: "ACR_ERR_NOT_CONVERGED", -5: "ACR_ERR_CUDA", -6: "ACR_ERR_TIMEOUT"}
 
@@ -50,7 +57,7 @@ class AcrError(RuntimeError):
 class acr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("input_kind", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("m_stop", ctypes.c_int), ("ir_tol", ctypes.c_double),
-                ("ir_max_iter", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("ir_max_iter", ctypes.c_int), ("stream", ctypes.c_void_p), ("refine", ctypes.c_int)]
 
 
 class acr_stats_t(ctypes.Structure):
@@ -60,7 +67,13 @@ class acr_stats_t(ctypes.Structure):
                 ("factor_flops", ctypes.c_double), ("factor_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("ir_iters", ctypes.c_int),
                 ("ir_resid_max", ctypes.c_double), ("rank_max", ctypes.c_int * 32),
-                ("rank_mean", ctypes.c_double * 32)]
+                ("rank_mean", ctypes.c_double * 32),
+                ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("inv_ms", ctypes.c_double), ("inv_flops", ctypes.c_double),
+                ("sweep_ms", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
+                ("gemm_launches", ctypes.c_longlong), ("inv_launches", ctypes.c_longlong),
+                ("sweep_launches", ctypes.c_longlong), ("launches_factor", ctypes.c_longlong),
+                ("launches_solve", ctypes.c_longlong)]
 
 
 def load(path: str = LIB_PATH):

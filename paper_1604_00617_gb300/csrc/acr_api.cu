@@ -120,6 +120,7 @@ struct acr_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool band0 = false;  // level 0 stored and reduced with its exact structure
     size_t es = 8;  // factor element size
     std::vector<Level> lev;
     DevBuf arena;   // persistent factors
@@ -148,10 +149,14 @@ void default_opts(acr_opts* o) {
     o->ir_tol = 1e-8;
     o->ir_max_iter = 20;
     o->stream = nullptr;
+    o->refine = ACR_REFINE_FGMRES;
 }
 
-// Level plan and persistent byte offsets.  Returns the arena size.
-size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev) {
+// Level plan and persistent byte offsets.  Returns the arena size.  With
+// band0 (5-point operator, level-0 A_i and C_i diagonal) level 0 keeps only
+// the diagonals: xa/xc hold a_j, c_j of the eliminated blocks (b values each;
+// D_j^-1 A_j is applied as D_j^-1 (a_j .* u)) and ak/ck those of the kept ones.
+size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev, bool band0 = false) {
     lev.clear();
     const size_t blk = (size_t)b * b * es;
     size_t off = 0;
@@ -162,11 +167,13 @@ size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev) {
         L.ne = (m + 1) / 2;
         L.nk = m / 2;
         const bool top = (m == 1);
+        const size_t ob = (band0 && m == n) ? (size_t)b * es : blk;  // off-diagonal storage per block
         L.off_dinv = off; off += L.ne * blk;
-        L.off_xa = off; off += top ? 0 : L.ne * blk;
-        L.off_xc = off; off += top ? 0 : L.ne * blk;
-        L.off_ak = off; off += L.nk * blk;
-        L.off_ck = off; off += L.nk * blk;
+        L.off_xa = off; off += top ? 0 : L.ne * ob;
+        L.off_xc = off; off += top ? 0 : L.ne * ob;
+        L.off_ak = off; off += L.nk * ob;
+        L.off_ck = off; off += L.nk * ob;
+        off = (off + 255) & ~(size_t)255;
         lev.push_back(L);
         if (top) break;
         m = m / 2;
@@ -174,12 +181,12 @@ size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev) {
     return off;
 }
 
-double factor_flops(const std::vector<Level>& lev, int b) {
-    // algorithmic flops of dense block cyclic reduction: 2 b^3 per block
-    // inverse, 2 b^3 per block product (D' has two)
+// Algorithmic flops of block cyclic reduction from level t0 on: 2 b^3 per
+// dense block inverse and per block product (D' has two).
+double factor_flops(const std::vector<Level>& lev, int b, size_t t0 = 0) {
     const double b3 = (double)b * b * b;
     double f = 0.0;
-    for (size_t t = 0; t < lev.size(); ++t) {
+    for (size_t t = t0; t < lev.size(); ++t) {
         const Level& L = lev[t];
         f += 2.0 * b3 * L.ne;
         if (L.m == 1) continue;
@@ -246,16 +253,39 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         h->st.operator_bytes = 3 * (size_t)n * bb * 8;
     }
 
+    // ---- level-0 structure: 5-point operator with diagonally dominant D_i ---
+    // (the tridiagonal inverse factors D_j without pivoting, which is stable
+    // for strictly row diagonally dominant tridiagonals; otherwise level 0 runs
+    // the general dense path)
+    h->band0 = false;
+    if (banded) {
+        std::vector<double> hD(nD);
+        CK(cudaMemcpyAsync(hD.data(), dD, nD * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool dom = true;
+        for (int i = 0; i < n && dom; ++i)
+            for (int r = 0; r < b; ++r) {
+                const double* Bk = hD.data() + (size_t)i * 3 * b;
+                const double off = (r > 0 ? std::fabs(Bk[r]) : 0.0) + (r + 1 < b ? std::fabs(Bk[2 * b + r]) : 0.0);
+                if (!(std::fabs(Bk[b + r]) > off)) { dom = false; break; }
+            }
+        h->band0 = dom;
+    }
+    const bool b0 = h->band0;
+
     // ---- persistent arena -------------------------------------------------
-    const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev);
+    const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev, b0);
     CK(h->arena.alloc_sync(arena_bytes));
     h->st.factor_bytes = arena_bytes;
     const int T_ = h->levels() - 1;
 
     // ---- temporaries: D_odd, A_even, C_even per level (ping-pong) ---------
-    auto temp_blocks = [&](const Level& L) { return (size_t)L.nk + 2 * (size_t)L.ne; };
+    auto temp_blocks = [&](int t) {
+        const Level& L = h->lev[t];
+        return (b0 && t == 0) ? (size_t)0 : (size_t)L.nk + 2 * (size_t)L.ne;
+    };
     size_t tmax[2] = {0, 0};
-    for (int t = 0; t <= T_; ++t) tmax[t & 1] = std::max(tmax[t & 1], temp_blocks(h->lev[t]));
+    for (int t = 0; t <= T_; ++t) tmax[t & 1] = std::max(tmax[t & 1], temp_blocks(t));
     DevBuf tmp[2];
     CK(tmp[0].alloc(tmax[0] * blk, s));
     CK(tmp[1].alloc(tmax[1] * blk, s));
@@ -276,7 +306,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     // ---- problem tables (built on the host, one upload) --------------------
     std::vector<GemmProb<T>> probs;
     std::vector<size_t> g1_off(T_ + 1), g1_cnt(T_ + 1), g2_off(T_ + 1), g2_cnt(T_ + 1);
-    for (int t = 0; t < T_; ++t) {
+    for (int t = (b0 ? 1 : 0); t < T_; ++t) {
         const Level& L = h->lev[t];
         const Level& Ln = h->lev[t + 1];
         T* dinv = h->P<T>(L.off_dinv);
@@ -326,17 +356,59 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     // ---- level 0 staging -----------------------------------------------------
     {
         const Level& L = h->lev[0];
-        CK(stage_level0<T>(banded ? 1 : 0, n, b, dA, dD, dC, h->P<T>(L.off_dinv), t_dodd(0), t_aev(0),
-                           h->P<T>(L.off_ak), t_cev(0), h->P<T>(L.off_ck), d_bad, s));
+        if (b0) {
+            const double* oa = h->op.as<double>() + 3 * (size_t)n * b;  // a with a_0 = 0
+            const double* oc = oa + (size_t)n * b;                       // c with c_{n-1} = 0
+            CK(stage_diagonals<T>(oa, oc, n, b, h->P<T>(L.off_xa), h->P<T>(L.off_xc), h->P<T>(L.off_ak),
+                                  h->P<T>(L.off_ck), d_bad, dD, s));
+        } else {
+            CK(stage_level0<T>(banded ? 1 : 0, n, b, dA, dD, dC, h->P<T>(L.off_dinv), t_dodd(0), t_aev(0),
+                               h->P<T>(L.off_ak), t_cev(0), h->P<T>(L.off_ck), d_bad, s));
+        }
     }
     const int use_tc = (h->prec == ACR_FP32TC_IR) ? 1 : 0;
     // ---- the reduction ---------------------------------------------------------
+    // per-class device time: one event pair around every inversion / product launch
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> evcls;  // 0: inversion, 1: products
+    auto mark = [&](int cls) -> cudaError_t {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        evs.push_back(e);
+        evcls.push_back(cls);
+        return cudaEventRecord(e, s);
+    };
+    const long long l0 = launch_count();
+    long long inv_l = 0, gemm_l = 0;
     for (int t = 0; t <= T_; ++t) {
         const Level& L = h->lev[t];
-        CK(gj_inverse<T>(h->P<T>(L.off_dinv), b, L.ne, dinfo.as<int>() + info_off[t], dpiv.as<int>(), s));
+        long long c0 = launch_count();
+        CK(mark(0));
+        if (b0 && t == 0)
+            CK(tridiag_inverse<T>(dD, n, b, h->P<T>(L.off_dinv), dinfo.as<int>() + info_off[t], s));
+        else
+            CK(gj_inverse<T>(h->P<T>(L.off_dinv), b, L.ne, dinfo.as<int>() + info_off[t], dpiv.as<int>(), s));
+        CK(mark(0));
+        inv_l += launch_count() - c0;
         if (t == T_) break;
+        if (b0 && t == 0) {
+            // elementwise Schur complement of the structured level 0
+            const Level& Ln = h->lev[1];
+            const double* oa = h->op.as<double>() + 3 * (size_t)n * b;
+            const double* oc = oa + (size_t)n * b;
+            CK(mark(2));
+            CK(schur_level0<T>(dD, oa, oc, n, b, h->P<T>(L.off_dinv), h->P<T>(Ln.off_dinv), t_dodd(1), t_aev(1),
+                               h->P<T>(Ln.off_ak), t_cev(1), h->P<T>(Ln.off_ck), s));
+            CK(mark(2));
+            continue;
+        }
+        c0 = launch_count();
+        CK(mark(1));
         CK(gemm_batched<T>(dp + g1_off[t], (int)g1_cnt[t], b, use_tc, s));
         CK(gemm_batched<T>(dp + g2_off[t], (int)g2_cnt[t], b, use_tc, s));
+        CK(mark(1));
+        gemm_l += launch_count() - c0;
     }
     CK(cudaEventRecord(e1, s));
     std::vector<int> info(ninfo + 1);
@@ -352,8 +424,32 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
             if (info[info_off[t] + e])
                 return fail(ACR_ERR_SINGULAR, "singular eliminated block: level %d, block %d (pivot %d)", t, 2 * e,
                             info[info_off[t] + e] - 1);
+    double cls_ms[3] = {0.0, 0.0, 0.0};
+    for (size_t i = 0; i + 1 < evs.size(); i += 2) {
+        float d = 0.f;
+        cudaEventElapsedTime(&d, evs[i], evs[i + 1]);
+        cls_ms[evcls[i]] += d;
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
     h->st.factor_ms = ms;
-    h->st.factor_flops = factor_flops(h->lev, b);
+    // structured level 0: O(b^2) per block (tridiagonal inverse: ~3 b^2;
+    // elementwise Schur complement: ~8 b^2 per kept block)
+    const size_t t0 = b0 ? 1 : 0;
+    double l0_inv = 0.0, l0_schur = 0.0;
+    if (b0) {
+        l0_inv = 3.0 * (double)b * b * h->lev[0].ne;
+        l0_schur = 8.0 * (double)b * b * h->lev[0].nk;
+    }
+    double inv_fl = l0_inv;
+    for (size_t t = t0; t < h->lev.size(); ++t) inv_fl += 2.0 * (double)b * b * b * h->lev[t].ne;
+    h->st.factor_flops = factor_flops(h->lev, b, t0) + l0_inv + l0_schur;
+    h->st.inv_ms = cls_ms[0];
+    h->st.inv_flops = inv_fl;
+    h->st.gemm_ms = cls_ms[1];
+    h->st.gemm_flops = h->st.factor_flops - inv_fl - l0_schur;
+    h->st.inv_launches = inv_l;
+    h->st.gemm_launches = gemm_l;
+    h->st.launches_factor = launch_count() - l0 + 1;  // + the staging kernel
     return ACR_OK;
 }
 
@@ -366,6 +462,20 @@ struct SweepPlan {
     DevBuf dprobs;
     std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
     int nrhs = 0;
+    double bytes = 0.0;             // algorithmic bytes of one pass
+    std::vector<cudaEvent_t> evs;   // start/end of every pass
+    long long launches = 0;
+    ~SweepPlan() { for (cudaEvent_t e : evs) cudaEventDestroy(e); }
+    double elapsed_ms() const {
+        double t = 0.0;
+        for (size_t i = 0; i + 1 < evs.size(); i += 2) {
+            float d = 0.f;
+            cudaEventElapsedTime(&d, evs[i], evs[i + 1]);
+            t += d;
+        }
+        return t;
+    }
+    int passes() const { return (int)(evs.size() / 2); }
 };
 
 template <class T>
@@ -416,9 +526,11 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
             for (int k = 0; k < L.nk; ++k) {
                 const int i = 2 * k + 1;
                 SweepProb<T> p = mk(Fp(t + 1) + (size_t)k * b, ldN, Fp(t) + (size_t)i * b, ldF, ldG, T(-1));
-                p.m[0] = ak + k * bb;
+                const size_t os = (h->band0 && t == 0) ? (size_t)b : bb;  // diagonal storage at level 0
+                if (h->band0 && t == 0) p.diag_mask = 3;
+                p.m[0] = ak + k * os;
                 p.x[0] = Gp(t) + (size_t)k * b;
-                if (i + 1 < L.m) { p.m[1] = ck + k * bb; p.x[1] = Gp(t) + (size_t)(k + 1) * b; }
+                if (i + 1 < L.m) { p.m[1] = ck + k * os; p.x[1] = Gp(t) + (size_t)(k + 1) * b; }
                 pr.push_back(p);
             }
         }
@@ -442,8 +554,16 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
                 } else {
                     const int e = i / 2;
                     SweepProb<T> p = mk(Fp(t) + (size_t)i * b, ldF, Gp(t) + (size_t)e * b, ldG, ldU, T(-1));
-                    if (i > 0) { p.m[0] = xa + e * bb; p.x[0] = Un + (size_t)((i - 2) / 2) * b; }
-                    if (i + 1 < L.m) { p.m[1] = xc + e * bb; p.x[1] = Un + (size_t)(i / 2) * b; }
+                    if (h->band0 && t == 0) {
+                        // u_j = g_j - D_j^-1 (a_j .* u_{j-1} + c_j .* u_{j+1})
+                        int nt = 0;
+                        if (i > 0) { p.x[nt] = Un + (size_t)((i - 2) / 2) * b; p.sx[nt] = xa + (size_t)e * b; ++nt; }
+                        if (i + 1 < L.m) { p.x[nt] = Un + (size_t)(i / 2) * b; p.sx[nt] = xc + (size_t)e * b; ++nt; }
+                        if (nt) p.m[0] = h->P<T>(L.off_dinv) + e * bb;
+                    } else {
+                        if (i > 0) { p.m[0] = xa + e * bb; p.x[0] = Un + (size_t)((i - 2) / 2) * b; }
+                        if (i + 1 < L.m) { p.m[1] = xc + e * bb; p.x[1] = Un + (size_t)(i / 2) * b; }
+                    }
                     pr.push_back(p);
                 }
             }
@@ -453,6 +573,20 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
     CK(sp.dprobs.alloc(pr.size() * sizeof(SweepProb<T>), s));
     CK(cudaMemcpyAsync(sp.dprobs.p, pr.data(), pr.size() * sizeof(SweepProb<T>), cudaMemcpyHostToDevice, s));
     sp.nrhs = nrhs;
+    // algorithmic traffic: every block read once, every panel operand read
+    // once and every output panel written once
+    const double pb = (double)b * nrhs * sizeof(T);
+    sp.bytes = 0.0;
+    for (const SweepProb<T>& p : pr) {
+        for (int t = 0; t < 3; ++t)
+            if (p.m[t]) sp.bytes += ((p.diag_mask >> t) & 1 ? (double)b * sizeof(T) : (double)bb * sizeof(T)) + pb;
+        if (p.sx[0]) {  // combined mode: second panel and the two scaling vectors
+            if (p.x[1]) sp.bytes += pb + (double)b * sizeof(T);
+            sp.bytes += (double)b * sizeof(T);
+        }
+        if (p.cin) sp.bytes += pb;
+        sp.bytes += pb;
+    }
     return ACR_OK;
 }
 
@@ -461,11 +595,20 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
     const int b = h->b, T_ = h->levels() - 1, nrhs = sp.nrhs;
     cudaStream_t s = h->stream;
     const SweepProb<T>* dp = sp.dprobs.template as<SweepProb<T>>();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    sp.evs.push_back(e0);
+    sp.evs.push_back(e1);
+    const long long c0 = launch_count();
+    CK(cudaEventRecord(e0, s));
     for (int t = 0; t <= T_; ++t) {
         CK(sweep_batched<T>(dp + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], b, nrhs, s));
         if (sp.fw_f_cnt[t]) CK(sweep_batched<T>(dp + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], b, nrhs, s));
     }
     for (int t = T_; t >= 0; --t) CK(sweep_batched<T>(dp + sp.bk_off[t], (int)sp.bk_cnt[t], b, nrhs, s));
+    CK(cudaEventRecord(e1, s));
+    sp.launches += launch_count() - c0;
     return ACR_OK;
 }
 
@@ -475,6 +618,7 @@ struct ResidPlan {
     int nprob = 0;
 };
 
+// f == NULL builds the plain product r = M x.
 int build_resid_dense(acr_ctx* h, const double* x, const double* f, double* r, int nrhs, ResidPlan& rp) {
     const int n = h->n, b = h->b;
     const size_t bb = h->bb();
@@ -487,8 +631,8 @@ int build_resid_dense(acr_ctx* h, const double* x, const double* f, double* r, i
         SweepProb<double> p;
         memset(&p, 0, sizeof(p));
         p.out = r + (size_t)i * b; p.ldo = N;
-        p.cin = f + (size_t)i * b; p.ldc = N;
-        p.ldx = N; p.alpha = -1.0;
+        p.cin = f ? f + (size_t)i * b : nullptr; p.ldc = N;
+        p.ldx = N; p.alpha = f ? -1.0 : 1.0;
         p.m[0] = oD + i * bb; p.x[0] = x + (size_t)i * b;
         if (i > 0) { p.m[1] = oA + i * bb; p.x[1] = x + (size_t)(i - 1) * b; }
         if (i + 1 < n) { p.m[2] = oC + i * bb; p.x[2] = x + (size_t)(i + 1) * b; }
@@ -512,6 +656,217 @@ int residual(acr_ctx* h, const double* x, const double* f, double* r, int nrhs, 
     return ACR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Refinement.  The preconditioner z = M^-1 v is one pass of the solve sweeps
+// in the factor's precision Tf; the residual and every Krylov quantity are
+// FP64 with the original operator.
+// ---------------------------------------------------------------------------
+template <class Tf>
+struct Precond {
+    acr_ctx* h = nullptr;
+    SweepPlan<Tf> sp;
+    DevBuf buf;
+    long long NQ = 0;
+    int init(acr_ctx* hh, int nrhs) {
+        h = hh;
+        NQ = (long long)h->n * h->b * nrhs;
+        CK(buf.alloc(NQ * sizeof(Tf), h->stream));
+        return build_sweep<Tf>(h, buf.as<Tf>(), nrhs, sp);
+    }
+    int apply(const double* v, double* z) {
+        cudaStream_t s = h->stream;
+        if constexpr (sizeof(Tf) == 4) {
+            CK(convert_d2f(v, buf.as<float>(), NQ, s));
+            int st = run_sweep<float>(h, sp);
+            if (st) return st;
+            CK(convert_f2d(buf.as<float>(), z, NQ, s));
+        } else {
+            CK(cudaMemcpyAsync(buf.p, v, NQ * 8, cudaMemcpyDeviceToDevice, s));
+            int st = run_sweep<double>(h, sp);
+            if (st) return st;
+            CK(cudaMemcpyAsync(z, buf.p, NQ * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        return ACR_OK;
+    }
+};
+
+// FP64 operator products on fixed buffers: res: r = f - M x;  mv: w = M z.
+struct Oper {
+    acr_ctx* h = nullptr;
+    int nrhs = 0;
+    const double *x = nullptr, *f = nullptr;
+    double *r = nullptr, *z = nullptr, *w = nullptr;
+    ResidPlan prs, pmv;
+    int init(acr_ctx* hh, const double* x_, const double* f_, double* r_, double* z_, double* w_, int nq) {
+        h = hh; x = x_; f = f_; r = r_; z = z_; w = w_; nrhs = nq;
+        if (h->in_kind != ACR_BANDED) {
+            int st = build_resid_dense(h, x, f, r, nrhs, prs);
+            if (st) return st;
+            if (z) return build_resid_dense(h, z, nullptr, w, nrhs, pmv);
+        }
+        return ACR_OK;
+    }
+    int res() { return residual(h, x, f, r, nrhs, &prs); }
+    int mv(const double* zin) {  // w = M zin (zin must be z for dense operators)
+        if (h->in_kind == ACR_BANDED) return residual(h, zin, nullptr, w, nrhs, nullptr);
+        if (zin != z) CK(cudaMemcpyAsync(z, zin, (size_t)h->n * h->b * nrhs * 8, cudaMemcpyDeviceToDevice, h->stream));
+        return residual(h, z, nullptr, w, nrhs, &pmv);
+    }
+};
+
+template <class Tf>
+int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std::vector<double>& rel,
+           int& iters) {
+    const long long N = (long long)h->n * h->b, NQ = N * nrhs;
+    cudaStream_t s = h->stream;
+    const double tol = h->opts.ir_tol;
+    const int maxit = std::max(1, h->opts.ir_max_iter);
+    const int method = h->opts.refine;
+    Precond<Tf> P;
+    int st = P.init(h, nrhs);
+    if (st) return st;
+    DevBuf r, zb, wb, ws, sq, coef;
+    CK(r.alloc(NQ * 8, s));
+    CK(zb.alloc(NQ * 8, s));
+    CK(wb.alloc(NQ * 8, s));
+    CK(ws.alloc((size_t)64 * nrhs * 1024 * 8, s));
+    CK(sq.alloc((size_t)64 * nrhs * 8, s));
+    CK(coef.alloc((size_t)64 * nrhs * 8, s));
+    Oper op;
+    if ((st = op.init(h, x, f, r.as<double>(), zb.as<double>(), wb.as<double>(), nrhs))) return st;
+    std::vector<double> fn2(nrhs), hs(64 * nrhs);
+    CK(col_sumsq(f, N, nrhs, ws.as<double>(), sq.as<double>(), s));
+    CK(cudaMemcpyAsync(fn2.data(), sq.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+    iters = 0;
+    if (!x0_given) {
+        if ((st = P.apply(f, x))) return st;
+        iters = 1;
+    }
+    auto check = [&](bool& conv) -> int {
+        int e = op.res();
+        if (e) return e;
+        CK(col_sumsq(r.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>(), s));
+        CK(cudaMemcpyAsync(hs.data(), sq.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        conv = true;
+        for (int q = 0; q < nrhs; ++q) {
+            rel[q] = fn2[q] > 0 ? std::sqrt(hs[q] / fn2[q]) : std::sqrt(hs[q]);
+            if (!(rel[q] <= tol)) conv = false;
+        }
+        return ACR_OK;
+    };
+    bool conv = false;
+    if ((st = check(conv))) return st;
+    if (conv || method == ACR_REFINE_NONE) return conv ? ACR_OK : fail(ACR_ERR_NOT_CONVERGED, "residual %g above ir_tol %g and refinement is off", *std::max_element(rel.begin(), rel.end()), tol);
+    if (method == ACR_REFINE_IR) {
+        while (iters < maxit && !conv) {
+            if ((st = P.apply(r.as<double>(), zb.as<double>()))) return st;
+            ++iters;
+            CK(add_d2d(x, zb.as<double>(), NQ, s));
+            if ((st = check(conv))) return st;
+        }
+    } else {
+        // restarted FGMRES(m), right preconditioned, one Krylov space per column
+        const int m = std::min(30, maxit);
+        DevBuf V, Z;
+        CK(V.alloc((size_t)(m + 1) * NQ * 8, s));
+        CK(Z.alloc((size_t)m * NQ * 8, s));
+        double* Vp = V.as<double>();
+        double* Zp = Z.as<double>();
+        std::vector<double> H((size_t)nrhs * (m + 1) * m), g((size_t)nrhs * (m + 1)), cs((size_t)nrhs * m),
+            sn((size_t)nrhs * m), sc(nrhs), hh((size_t)(m + 1) * nrhs), y((size_t)m * nrhs);
+        auto Hq = [&](int q, int i, int j) -> double& { return H[((size_t)q * (m + 1) + i) * m + j]; };
+        while (iters < maxit && !conv) {
+            std::fill(H.begin(), H.end(), 0.0);
+            std::fill(g.begin(), g.end(), 0.0);
+            for (int q = 0; q < nrhs; ++q) {
+                const double beta = std::sqrt(hs[q]);
+                g[(size_t)q * (m + 1)] = beta;
+                sc[q] = beta > 0 ? 1.0 / beta : 0.0;
+            }
+            CK(cudaMemcpyAsync(coef.p, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, s));
+            CK(col_scale(Vp, r.as<double>(), coef.as<double>(), N, nrhs, s));
+            int jd = 0;
+            for (int j = 0; j < m && iters < maxit; ++j) {
+                double* Vj = Vp + (size_t)j * NQ;
+                double* Zj = Zp + (size_t)j * NQ;
+                if ((st = P.apply(Vj, Zj))) return st;
+                ++iters;
+                if ((st = op.mv(Zj))) return st;
+                double* w = wb.as<double>();
+                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                    CK(multi_dot(Vp, j + 1, w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
+                    CK(cudaMemcpyAsync(hh.data(), sq.p, (size_t)(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    for (int i = 0; i <= j; ++i)
+                        for (int q = 0; q < nrhs; ++q) {
+                            Hq(q, i, j) += hh[(size_t)i * nrhs + q];
+                            hh[(size_t)i * nrhs + q] = -hh[(size_t)i * nrhs + q];
+                        }
+                    CK(cudaMemcpyAsync(coef.p, hh.data(), (size_t)(j + 1) * nrhs * 8, cudaMemcpyHostToDevice, s));
+                    CK(multi_axpy(w, Vp, j + 1, coef.as<double>(), N, nrhs, s));
+                }
+                CK(col_sumsq(w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
+                CK(cudaMemcpyAsync(hs.data(), sq.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                bool all = true;
+                for (int q = 0; q < nrhs; ++q) {
+                    const double hn = std::sqrt(hs[q]);
+                    Hq(q, j + 1, j) = hn;
+                    sc[q] = hn > 0 ? 1.0 / hn : 0.0;
+                    // Givens rotations on column j of this column's Hessenberg
+                    for (int i = 0; i < j; ++i) {
+                        const double c = cs[(size_t)q * m + i], sv = sn[(size_t)q * m + i];
+                        const double a = Hq(q, i, j), bq = Hq(q, i + 1, j);
+                        Hq(q, i, j) = c * a + sv * bq;
+                        Hq(q, i + 1, j) = -sv * a + c * bq;
+                    }
+                    const double a = Hq(q, j, j), bq = Hq(q, j + 1, j);
+                    const double rr = std::hypot(a, bq);
+                    const double c = rr > 0 ? a / rr : 1.0, sv = rr > 0 ? bq / rr : 0.0;
+                    cs[(size_t)q * m + j] = c;
+                    sn[(size_t)q * m + j] = sv;
+                    Hq(q, j, j) = rr;
+                    Hq(q, j + 1, j) = 0.0;
+                    double* gq = &g[(size_t)q * (m + 1)];
+                    gq[j + 1] = -sv * gq[j];
+                    gq[j] = c * gq[j];
+                    const double est = fn2[q] > 0 ? std::fabs(gq[j + 1]) / std::sqrt(fn2[q]) : std::fabs(gq[j + 1]);
+                    if (!(est <= 0.5 * tol)) all = false;
+                }
+                CK(cudaMemcpyAsync(coef.p, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, s));
+                CK(col_scale(Vp + (size_t)(j + 1) * NQ, w, coef.as<double>(), N, nrhs, s));
+                jd = j + 1;
+                if (all) break;
+            }
+            // y = R^-1 g per column, x += Z y
+            for (int q = 0; q < nrhs; ++q) {
+                const double* gq = &g[(size_t)q * (m + 1)];
+                for (int i = jd - 1; i >= 0; --i) {
+                    double t = gq[i];
+                    for (int k = i + 1; k < jd; ++k) t -= Hq(q, i, k) * y[(size_t)k * nrhs + q];
+                    const double d = Hq(q, i, i);
+                    y[(size_t)i * nrhs + q] = std::fabs(d) > 0 ? t / d : 0.0;
+                }
+            }
+            CK(cudaMemcpyAsync(coef.p, y.data(), (size_t)jd * nrhs * 8, cudaMemcpyHostToDevice, s));
+            CK(multi_axpy(x, Zp, jd, coef.as<double>(), N, nrhs, s));
+            if ((st = check(conv))) return st;
+        }
+    }
+    {
+        CK(cudaStreamSynchronize(s));
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->st.sweep_ms += P.sp.elapsed_ms();
+        h->st.sweep_bytes += P.sp.bytes * P.sp.passes();
+        h->st.sweep_launches += P.sp.launches;
+    }
+    if (!conv)
+        return fail(ACR_ERR_NOT_CONVERGED, "refinement took %d preconditioner solves without ||r||/||b|| <= %g (worst %g)",
+                    iters, tol, *std::max_element(rel.begin(), rel.end()));
+    return ACR_OK;
+}
+
 int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_out) {
     const int n = h->n, b = h->b;
     const long long N = (long long)n * b;
@@ -528,77 +883,38 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
         CK(cudaMemcpyAsync(dB.p, B, bytes, cudaMemcpyHostToDevice, s));
         f = dB.as<double>();
     }
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->st.sweep_ms = 0.0;
+        h->st.sweep_bytes = 0.0;
+        h->st.sweep_launches = 0;
+    }
+    const long long lc0 = launch_count();
     CK(cudaEventRecord(e0, s));
-    int iters = 0;
-    int status = ACR_OK;
+    int iters = 0, status = ACR_OK;
     std::vector<double> rel(nrhs, 0.0);
-    const bool want_resid = resid_out != nullptr;
-    if (h->prec == ACR_FP64) {
-        // FP64 sweeps in place; keep f for the residual if asked for
-        DevBuf f0, r, ws, sq;
-        double* x = f;
-        if (want_resid) {
-            CK(f0.alloc(bytes, s));
-            CK(cudaMemcpyAsync(f0.p, f, bytes, cudaMemcpyDeviceToDevice, s));
-        }
-        SweepPlan<double> sp;
-        int st = build_sweep<double>(h, x, nrhs, sp);
-        if (st) return st;
-        st = run_sweep<double>(h, sp);
-        if (st) return st;
-        if (want_resid) {
-            CK(r.alloc(bytes, s));
-            CK(ws.alloc((size_t)nrhs * 1024 * 8, s));
-            CK(sq.alloc((size_t)nrhs * 2 * 8, s));
-            ResidPlan rp;
-            if (h->in_kind != ACR_BANDED && (st = build_resid_dense(h, x, f0.as<double>(), r.as<double>(), nrhs, rp))) return st;
-            if ((st = residual(h, x, f0.as<double>(), r.as<double>(), nrhs, &rp))) return st;
-            CK(col_sumsq(r.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>(), s));
-            CK(col_sumsq(f0.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>() + nrhs, s));
-            std::vector<double> hs(2 * nrhs);
-            CK(cudaMemcpyAsync(hs.data(), sq.p, 2 * nrhs * 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int q = 0; q < nrhs; ++q) rel[q] = hs[nrhs + q] > 0 ? std::sqrt(hs[q] / hs[nrhs + q]) : std::sqrt(hs[q]);
-        }
-    } else {
-        // mixed precision: FP32 sweeps, FP64 residual and correction
-        DevBuf x, r, f32, ws, sq;
+    {
+        DevBuf x, f0;
         CK(x.alloc(bytes, s));
-        CK(r.alloc(bytes, s));
-        CK(f32.alloc((size_t)N * nrhs * 4, s));
-        CK(ws.alloc((size_t)nrhs * 1024 * 8, s));
-        CK(sq.alloc((size_t)nrhs * 2 * 8, s));
-        CK(cudaMemsetAsync(x.p, 0, bytes, s));
-        CK(cudaMemcpyAsync(r.p, f, bytes, cudaMemcpyDeviceToDevice, s));
-        CK(col_sumsq(f, N, nrhs, ws.as<double>(), sq.as<double>() + nrhs, s));
-        SweepPlan<float> sp;
-        int st = build_sweep<float>(h, f32.as<float>(), nrhs, sp);
-        if (st) return st;
-        ResidPlan rp;
-        if (h->in_kind != ACR_BANDED && (st = build_resid_dense(h, x.as<double>(), f, r.as<double>(), nrhs, rp))) return st;
-        std::vector<double> hs(2 * nrhs);
-        const int maxit = std::max(1, h->opts.ir_max_iter);
-        const double tol = h->opts.ir_tol;
-        bool conv = false;
-        for (iters = 1; iters <= maxit; ++iters) {
-            CK(convert_d2f(r.as<double>(), f32.as<float>(), (long long)N * nrhs, s));
-            if ((st = run_sweep<float>(h, sp))) return st;
-            CK(add_f2d(x.as<double>(), f32.as<float>(), (long long)N * nrhs, s));
-            if ((st = residual(h, x.as<double>(), f, r.as<double>(), nrhs, &rp))) return st;
-            CK(col_sumsq(r.as<double>(), N, nrhs, ws.as<double>(), sq.as<double>(), s));
-            CK(cudaMemcpyAsync(hs.data(), sq.p, 2 * nrhs * 8, cudaMemcpyDeviceToHost, s));
+        if (h->prec == ACR_FP64) {
+            // direct FP64 sweep; refinement only if the residual misses ir_tol
+            SweepPlan<double> sp;
+            int st = build_sweep<double>(h, x.as<double>(), nrhs, sp);
+            if (st) return st;
+            CK(cudaMemcpyAsync(x.p, f, bytes, cudaMemcpyDeviceToDevice, s));
+            if ((st = run_sweep<double>(h, sp))) return st;
             CK(cudaStreamSynchronize(s));
-            conv = true;
-            for (int q = 0; q < nrhs; ++q) {
-                rel[q] = hs[nrhs + q] > 0 ? std::sqrt(hs[q] / hs[nrhs + q]) : std::sqrt(hs[q]);
-                if (!(rel[q] <= tol)) conv = false;
+            {
+                std::lock_guard<std::mutex> lk(h->mu);
+                h->st.sweep_ms += sp.elapsed_ms();
+                h->st.sweep_bytes += sp.bytes;
+                h->st.sweep_launches += sp.launches;
             }
-            if (conv) break;
+            status = refine<double>(h, f, x.as<double>(), nrhs, true, rel, iters);
+        } else {
+            status = refine<float>(h, f, x.as<double>(), nrhs, false, rel, iters);
         }
-        if (!conv) {
-            iters = maxit;
-            status = fail(ACR_ERR_NOT_CONVERGED, "refinement reached %d iterations without ||r||/||b|| <= %g", maxit, tol);
-        }
+        if (status != ACR_OK && status != ACR_ERR_NOT_CONVERGED) return status;
         CK(cudaMemcpyAsync(f, x.p, bytes, cudaMemcpyDeviceToDevice, s));
     }
     CK(cudaEventRecord(e1, s));
@@ -611,13 +927,14 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
     {
         std::lock_guard<std::mutex> lk(h->mu);
         h->st.solve_ms = ms;
-        h->st.ir_iters = h->prec == ACR_FP64 ? 0 : iters;
+        h->st.launches_solve = launch_count() - lc0;
+        h->st.ir_iters = iters;
         double mx = 0.0;
         for (double v : rel) mx = std::max(mx, v);
         h->st.ir_resid_max = mx;
     }
     if (resid_out) memcpy(resid_out, rel.data(), sizeof(double) * nrhs);
-    if (iters_out) *iters_out = h->prec == ACR_FP64 ? 0 : iters;
+    if (iters_out) *iters_out = iters;
     return status;
 }
 

@@ -8,6 +8,11 @@
 
 namespace acr {
 
+// Kernel launches issued by this library (all threads); the C ABI reports
+// per-call deltas.
+long long launch_count();
+void count_launches(int k);
+
 // One batched block product: out = beta * cin + alpha * sum_t a[t] * bm[t],
 // every operand a blksz x blksz column-major block (leading dimension blksz).
 // A NULL a[t] drops term t; a NULL cin means beta is ignored.
@@ -26,16 +31,43 @@ struct GemmProb {
 // diag_mask is set, the blksz diagonal of a diagonal block;  x[t], cin, out
 // blksz-row panels with leading dimensions ldx, ldc, ldo.  cin may be NULL
 // (treated as zero).  A NULL m[t] drops term t.
+//
+// Combined mode (sx[0] != NULL): only m[0] is applied, to the scaled sum
+//   sx[0] .* x[0] + sx[1] .* x[1]    (sx[t] blksz-vectors; x[1], sx[1] may be NULL)
+// which is the level-0 back-substitution D_j^-1 (a_j .* u_{j-1} + c_j .* u_{j+1})
+// when A_j, C_j are diagonal.
 template <class T>
 struct SweepProb {
     T* out;
     const T* cin;
     const T* m[3];
     const T* x[3];
+    const T* sx[2];
     long long ldo, ldc, ldx;
     T alpha;
     int diag_mask;
 };
+
+// --- level 0 of a banded (5-point) operator -----------------------------------
+// Inverse of each tridiagonal D_j, j even: rows computed by the two bidiagonal
+// solves of the LU factorization (no pivoting; used only when every D_j is
+// strictly diagonally dominant by rows, where that factorization is stable).
+// Dband: FP64 [sub, diag, super] per block (3b), dinv: ne blocks.
+template <class T>
+cudaError_t tridiag_inverse(const double* Dband, int n, int b, T* dinv, int* info, cudaStream_t s);
+// Schur complement of level 0 with diagonal A_i, C_i (elementwise):
+//   D'_k = D_i - a_i .* Dinv_{i-1} .* c_{i-1}^T - c_i .* Dinv_{i+1} .* a_{i+1}^T
+//   A'_k = -a_i .* Dinv_{i-1} .* a_{i-1}^T,   C'_k = -c_i .* Dinv_{i+1} .* c_{i+1}^T
+// outputs routed like the dense path (k even -> nd/na/nc_even, k odd -> *_odd).
+template <class T>
+cudaError_t schur_level0(const double* Dband, const double* a, const double* c, int n, int b,
+                         const T* dinv, T* nd_even, T* nd_odd, T* na_even, T* na_odd, T* nc_even,
+                         T* nc_odd, cudaStream_t s);
+// Route the diagonals of A_j, C_j (FP64, b per block) to T arrays:
+// even j -> aev/cev[j/2], odd i -> ak/ck[i/2].
+template <class T>
+cudaError_t stage_diagonals(const double* a, const double* c, int n, int b, T* aev, T* cev, T* ak,
+                            T* ck, int* bad, const double* Dband, cudaStream_t s);
 
 // --- batched Gauss-Jordan inversion with partial pivoting (in place) -------
 // mats: count blocks of b x b (stride b*b).  info[e] is set to k+1 for the
@@ -77,5 +109,17 @@ cudaError_t convert_d2f(const double* src, float* dst, long long n, cudaStream_t
 cudaError_t add_f2d(double* x, const float* d, long long n, cudaStream_t s);
 // x += d
 cudaError_t add_d2d(double* x, const double* d, long long n, cudaStream_t s);
+// dst = (double) src
+cudaError_t convert_f2d(const float* src, double* dst, long long n, cudaStream_t s);
+// Krylov helpers on nvec column blocks V_i = V + i * N * nrhs (each N x nrhs):
+//   out[i * nrhs + q] = sum_r V_i[r, q] w[r, q]        (i < nvec), deterministic
+cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws,
+                      double* out, cudaStream_t s);
+//   w[r, q] += sum_i coef[i * nrhs + q] V_i[r, q]
+cudaError_t multi_axpy(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
+                       cudaStream_t s);
+//   v[r, q] = w[r, q] * scale[q]
+cudaError_t col_scale(double* v, const double* w, const double* scale, long long N, int nrhs,
+                      cudaStream_t s);
 
 }  // namespace acr

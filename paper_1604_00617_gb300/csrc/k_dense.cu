@@ -12,12 +12,18 @@
 //    column norms, conversions).
 //
 // All blocks are column-major with leading dimension b.
+#include <algorithm>
 #include <cfloat>
+#include <atomic>
 #include <cmath>
 
 #include "acr_internal.h"
 
 namespace acr {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launches(int k) { g_launches.fetch_add(k); }
 
 template <class T> struct Lim;
 template <> struct Lim<float> { static __device__ __forceinline__ float eps() { return FLT_EPSILON; } };
@@ -25,6 +31,18 @@ template <> struct Lim<double> { static __device__ __forceinline__ double eps() 
 
 template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 template <class T> __device__ __forceinline__ bool tfinite(T x) { return isfinite(x); }
+
+// 16-byte vectors of T
+template <class T, int V> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <class VT, class T> __device__ __forceinline__ T vget(const VT& v, int i);
+template <> __device__ __forceinline__ float vget<float4, float>(const float4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double2, double>(const double2& v, int i) {
+    return i == 0 ? v.x : v.y;
+}
 
 // Block-wide reduction helpers (blockDim.x multiple of 32, <= 1024).
 template <class T>
@@ -207,6 +225,95 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
     if (tid == 0 && first_bad && info[blockIdx.x] == 0) info[blockIdx.x] = first_bad;
 }
 
+// Register-resident panel step: thread t owns panel rows t, t+NT, ... (RPT of
+// them, KB values each, in registers).  Per pivot: block arg-max of the pivot
+// column, the owners of rows k and p publish them through shared memory, then
+// every thread applies the GJ step to its own rows.  Same arithmetic as
+// k_gj_panel.
+template <class T, int NT, int RPT, int KB>
+__global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b, int k0,
+                                                     int* __restrict__ pivs, int* __restrict__ info,
+                                                     const T* __restrict__ amax_in) {
+    __shared__ T rv[32];
+    __shared__ int ri[32];
+    __shared__ T sp[KB];
+    __shared__ T sk[KB];
+    T* G = mats + (size_t)blockIdx.x * b * b;
+    int* piv = pivs + (size_t)blockIdx.x * b;
+    const int tid = threadIdx.x;
+    T v[RPT][KB];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int r = tid + i * NT;
+#pragma unroll
+        for (int c = 0; c < KB; ++c) v[i][c] = (r < b) ? G[r + (size_t)(k0 + c) * b] : T(0);
+    }
+    const T tiny = T(16) * Lim<T>::eps() * amax_in[blockIdx.x];
+    int first_bad = 0;
+#pragma unroll
+    for (int kk = 0; kk < KB; ++kk) {
+        const int k = k0 + kk;
+        T val = T(-1);
+        int idx = 0x7fffffff;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int r = tid + i * NT;
+            if (r >= k && r < b) {
+                const T a = tabs(v[i][kk]);
+                if (a > val) { val = a; idx = r; }
+            }
+        }
+        block_argmax(val, idx, rv, ri);
+        const int p = (idx < b) ? idx : k;
+        const bool bad = !(val > tiny) || !tfinite(val);
+        if (bad && first_bad == 0) first_bad = k + 1;
+        if (tid == 0) piv[k] = p;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int r = tid + i * NT;
+            if (r == p) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) sp[c] = v[i][c];
+            }
+            if (r == k) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) sk[c] = v[i][c];
+            }
+        }
+        __syncthreads();
+        const T inv = bad ? T(1) : T(1) / sp[kk];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int r = tid + i * NT;
+            if (r >= b) continue;
+            if (r == k) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) v[i][c] = (c == kk) ? inv : sp[c] * inv;
+            } else {
+                if (r == p) {
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) v[i][c] = sk[c];
+                }
+                const T f = v[i][kk];
+                const T fi = f * inv;
+#pragma unroll
+                for (int c = 0; c < KB; ++c)
+                    if (c != kk) v[i][c] -= fi * sp[c];
+                v[i][kk] = -fi;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int r = tid + i * NT;
+        if (r < b) {
+#pragma unroll
+            for (int c = 0; c < KB; ++c) G[r + (size_t)(k0 + c) * b] = v[i][c];
+        }
+    }
+    if (tid == 0 && first_bad && info[blockIdx.x] == 0) info[blockIdx.x] = first_bad;
+}
+
 template <class T, int NT, int JT>
 __global__ void __launch_bounds__(NT) k_gj_update(T* __restrict__ mats, int b, int k0, int kb,
                                                   const int* __restrict__ pivs) {
@@ -281,6 +388,295 @@ __global__ void __launch_bounds__(NT) k_gj_update(T* __restrict__ mats, int b, i
     }
 }
 
+// Tiled update step: the same arithmetic as k_gj_update, organised as a GEMM
+// with K = kb.  One CTA owns a strip of BN columns of J (all rows, so the
+// in-place row interchange is race-free: the displaced rows of the strip are
+// read into shared memory first).  Row tiles of BM rows are streamed:
+//   acc = Panel[rows, K] * (P M)[K, strip]          (BM x BN, TM x TN per thread)
+//   M[r, strip] = base(r) + acc,  base = 0 (r in K) | (P M)[r, strip]
+template <class T, int BM, int BN, int TM, int TN, int KBMAX>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gj_update_tiled(T* __restrict__ mats, int b, int k0, int kb, const int* __restrict__ pivs) {
+    constexpr int RY = BM / TM, RX = BN / TN, NT = RY * RX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* stash = reinterpret_cast<T*>(smem_raw);           // [2*KBMAX][BN]: slot s, column j
+    T* Ps = stash + 2 * KBMAX * BN;                       // [KBMAX][BM]: panel tile, k-major
+    int* perm = reinterpret_cast<int*>(Ps + KBMAX * BM);  // b
+    int* slot = perm + b;                                 // b
+    int* list = slot + b;                                 // KBMAX
+    __shared__ int s_cnt;
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* piv = pivs + (size_t)blockIdx.y * b;
+    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    const int nJ = b - kb;
+    const int j0 = blockIdx.x * BN;
+    for (int r = tid; r < b; r += NT) { perm[r] = r; slot[r] = -1; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int kk = 0; kk < kb; ++kk) {
+            const int k = k0 + kk, p = piv[k];
+            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+            slot[k] = kk;
+        }
+        int cnt = 0;
+        for (int kk = 0; kk < kb; ++kk) {
+            const int p = piv[k0 + kk];
+            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
+        }
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    const int ns = kb + s_cnt;
+    // displaced rows of this strip (slots < kb are the interchanged pivot rows)
+    for (int i = tid; i < ns * BN; i += NT) {
+        const int s = i / BN, j = i % BN;
+        const int jc = j0 + j;
+        T v = T(0);
+        if (jc < nJ) {
+            const int c = jc < k0 ? jc : jc + kb;
+            const int r = s < kb ? k0 + s : list[s - kb];
+            v = G[perm[r] + (size_t)c * b];
+        }
+        stash[s * BN + j] = v;
+    }
+    int cidx[TN];
+    bool cok[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int jc = j0 + tx + j * RX;
+        cok[j] = jc < nJ;
+        cidx[j] = jc < k0 ? jc : jc + kb;
+    }
+    for (int row0 = 0; row0 < b; row0 += BM) {
+        __syncthreads();  // stash written / previous Ps reads done
+        for (int i = tid; i < kb * BM; i += NT) {
+            const int r = i % BM, k = i / BM;
+            const int gr = row0 + r;
+            Ps[k * BM + r] = (gr < b) ? G[gr + (size_t)(k0 + k) * b] : T(0);
+        }
+        __syncthreads();
+        T acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+        for (int k = 0; k < kb; ++k) {
+            T af[TM], bf[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) af[i] = Ps[k * BM + ty + i * RY];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bf[j] = stash[k * BN + tx + j * RX];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + ty + i * RY;
+            if (r >= b) continue;
+            const int sl = slot[r];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                if (!cok[j]) continue;
+                const size_t o = r + (size_t)cidx[j] * b;
+                const T base = (sl < 0) ? G[o] : (sl < kb ? T(0) : stash[sl * BN + tx + j * RX]);
+                G[o] = base + acc[i][j];
+            }
+        }
+    }
+}
+
+// Two-kernel update for full parallelism over (row tile, column tile, block).
+// gather: the rows that the panel's interchanges move (the kb pivot rows K
+// and the rows they were swapped with) are copied, after interchange, to a
+// stash (slot s, all b columns); slot map: -1 (row unchanged), s < kb (row in
+// K: base 0, stash row s is (P M)[K]), s >= kb (displaced row: base = stash).
+template <class T>
+__global__ void k_gj_gather(const T* __restrict__ mats, int b, int k0, int kb, const int* __restrict__ pivs,
+                            T* __restrict__ stash, int* __restrict__ slotmap) {
+    extern __shared__ int sh_i[];
+    int* perm = sh_i;        // b
+    int* slot = perm + b;    // b
+    int* list = slot + b;    // kb
+    __shared__ int s_cnt;
+    const T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* piv = pivs + (size_t)blockIdx.y * b;
+    T* st = stash + (size_t)blockIdx.y * 2 * kb * b;
+    for (int r = threadIdx.x; r < b; r += blockDim.x) { perm[r] = r; slot[r] = -1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int kk = 0; kk < kb; ++kk) {
+            const int k = k0 + kk, p = piv[k];
+            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+            slot[k] = kk;
+        }
+        int cnt = 0;
+        for (int kk = 0; kk < kb; ++kk) {
+            const int p = piv[k0 + kk];
+            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
+        }
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    const int ns = kb + s_cnt;
+    if (blockIdx.x == 0)
+        for (int r = threadIdx.x; r < b; r += blockDim.x) slotmap[(size_t)blockIdx.y * b + r] = slot[r];
+    const int c0 = blockIdx.x * 64;
+    for (int i = threadIdx.x; i < ns * 64; i += blockDim.x) {
+        const int s = i % ns, j = i / ns, c = c0 + j;
+        if (c >= b) continue;
+        const int r = s < kb ? k0 + s : list[s - kb];
+        st[(size_t)s * b + c] = G[perm[r] + (size_t)c * b];
+    }
+}
+
+// update: acc = Panel[rows, K] * stash[0:kb, cols] over the columns outside K.
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict__ stash,
+                const int* __restrict__ slotmap, int tiles_m) {
+    constexpr int RY = BM / TM, RX = BN / TN, NT = RY * RX;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN + 1];
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const T* st = stash + (size_t)blockIdx.y * 2 * kb * b;
+    const int* slot = slotmap + (size_t)blockIdx.y * b;
+    const int nJ = b - kb;
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int row0 = tm * BM, j0 = tn * BN;
+    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int kq = 0; kq < kb; kq += BK) {
+        for (int i = tid; i < BM * BK; i += NT) {
+            const int r = i % BM, k = i / BM;
+            const int gr = row0 + r;
+            As[k][r] = (gr < b && kq + k < kb) ? G[gr + (size_t)(k0 + kq + k) * b] : T(0);
+        }
+        for (int i = tid; i < BK * BN; i += NT) {
+            const int j = i % BN, k = i / BN;
+            const int jc = j0 + j;
+            const int c = jc < k0 ? jc : jc + kb;
+            Bs[k][j] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            T af[TM], bf[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) af[i] = As[k][ty + i * RY];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bf[j] = Bs[k][tx + j * RX];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int jc = j0 + tx + j * RX;
+        if (jc >= nJ) continue;
+        const int c = jc < k0 ? jc : jc + kb;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + ty + i * RY;
+            if (r >= b) continue;
+            const int sl = slot[r];
+            const size_t o = r + (size_t)c * b;
+            const T base = (sl < 0) ? G[o] : (sl < kb ? T(0) : st[(size_t)sl * b + c]);
+            G[o] = base + acc[i][j];
+        }
+    }
+}
+
+// Same update with V consecutive rows per thread (16-byte vector access of
+// the b x b block in the epilogue; a warp covers 32*V consecutive rows of one
+// column).  Tile BM x BN, TN columns per thread.
+template <class T, int V, int BM, int BN, int BK, int TN>
+__global__ void __launch_bounds__((BM / V) * (BN / TN))
+k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict__ stash,
+                const int* __restrict__ slotmap, int tiles_m) {
+    using VT = typename VecT<T, V>::type;
+    constexpr int RY = BM / V, RX = BN / TN, NT = RY * RX;
+    __shared__ __align__(16) T As[BK][BM];
+    __shared__ T Bs[BK][BN + 1];
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const T* st = stash + (size_t)blockIdx.y * 2 * kb * b;
+    const int* slot = slotmap + (size_t)blockIdx.y * b;
+    const int nJ = b - kb;
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int row0 = tm * BM, j0 = tn * BN;
+    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    const int rbase = row0 + ty * V;
+    T acc[V][TN];
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int kq = 0; kq < kb; kq += BK) {
+        for (int i = tid; i < BM * BK; i += NT) {
+            const int r = i % BM, k = i / BM;
+            const int gr = row0 + r;
+            As[k][r] = (gr < b && kq + k < kb) ? G[gr + (size_t)(k0 + kq + k) * b] : T(0);
+        }
+        for (int i = tid; i < BK * BN; i += NT) {
+            const int j = i % BN, k = i / BN;
+            const int jc = j0 + j;
+            const int c = jc < k0 ? jc : jc + kb;
+            Bs[k][j] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const VT av = *reinterpret_cast<const VT*>(&As[k][ty * V]);
+            T bf[TN];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bf[j] = Bs[k][tx + j * RX];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T a = vget<VT, T>(av, i);
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a, bf[j], acc[i][j]);
+            }
+        }
+        __syncthreads();
+    }
+    if (rbase >= b) return;
+    int sl[V];
+    bool plain = true;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        sl[i] = slot[rbase + i];
+        plain &= sl[i] < 0;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int jc = j0 + tx + j * RX;
+        if (jc >= nJ) continue;
+        const int c = jc < k0 ? jc : jc + kb;
+        T* gp = G + rbase + (size_t)c * b;
+        if (plain) {
+            VT v = *reinterpret_cast<const VT*>(gp);
+            T* pv = reinterpret_cast<T*>(&v);
+#pragma unroll
+            for (int i = 0; i < V; ++i) pv[i] += acc[i][j];
+            *reinterpret_cast<VT*>(gp) = v;
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const T base = (sl[i] < 0) ? gp[i] : (sl[i] < kb ? T(0) : st[(size_t)sl[i] * b + c]);
+                gp[i] = base + acc[i][j];
+            }
+        }
+    }
+}
+
 // Column interchanges in reverse order, one thread per row.
 template <class T>
 __global__ void k_gj_unscramble(T* __restrict__ mats, int b, const int* __restrict__ pivs) {
@@ -301,20 +697,31 @@ __global__ void k_gj_unscramble(T* __restrict__ mats, int b, const int* __restri
     }
 }
 
+// max |entry| per block; grid (chunks, count), combined with an integer
+// atomicMax on the IEEE bits (order-preserving for values >= 0); a NaN or Inf
+// entry gives +Inf.  out must be zeroed first.
+__device__ __forceinline__ void atomic_max_pos(float* a, float v) {
+    atomicMax(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_pos(double* a, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
 template <class T>
 __global__ void k_maxabs(const T* __restrict__ mats, int b, T* __restrict__ out) {
     __shared__ T red[32];
-    const T* G = mats + (size_t)blockIdx.x * b * b;
+    const T* G = mats + (size_t)blockIdx.y * b * b;
+    const size_t bb = (size_t)b * b;
     T m = T(0);
     bool fin = true;
-    for (size_t i = threadIdx.x; i < (size_t)b * b; i += blockDim.x) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bb; i += (size_t)gridDim.x * blockDim.x) {
         const T v = G[i];
         fin &= tfinite(v);
         m = fmax(m, tabs(v));
     }
     if (!fin) m = T(INFINITY);
     m = block_max(m, red);
-    if (threadIdx.x == 0) out[blockIdx.x] = m;
+    if (threadIdx.x == 0) atomic_max_pos(out + blockIdx.y, m);
 }
 
 template <class T>
@@ -331,6 +738,7 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
         auto kern = k_gj_small<T, 256>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
         kern<<<count, 256, small, s>>>(mats, b, info);
+        count_launches(1);
         return cudaGetLastError();
     }
     // blocked path
@@ -338,26 +746,63 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
     T* amax = nullptr;
     cudaError_t e = cudaMallocAsync(&amax, sizeof(T) * count, s);
     if (e != cudaSuccess) return e;
-    k_maxabs<T><<<count, 256, 0, s>>>(mats, b, amax);
+    cudaMemsetAsync(amax, 0, sizeof(T) * count, s);
+    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
+    count_launches(1);
     constexpr int JT = 16;
+    constexpr int KB = sizeof(T) == 8 ? 16 : 32;
     const size_t psmem = (size_t)b * kb * sizeof(T);
     const size_t usmem = (size_t)2 * kb * JT * sizeof(T) + (2 * (size_t)b + kb) * sizeof(int);
     auto kp = k_gj_panel<T, 512>;
     auto ku = k_gj_update<T, 256, JT>;
     cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+    const int rpt = (b + 511) / 512;
+    // stash of interchanged rows + slot map for the parallel update
+    T* stash = nullptr;
+    int* slotmap = nullptr;
+    if (cudaMallocAsync(&stash, sizeof(T) * (size_t)count * 2 * kb * b + sizeof(int) * (size_t)count * b, s) ==
+        cudaSuccess)
+        slotmap = reinterpret_cast<int*>(stash + (size_t)count * 2 * kb * b);
+    else
+        cudaGetLastError(), stash = nullptr;
     for (int k0 = 0; k0 < b; k0 += kb) {
         const int kbi = (b - k0) < kb ? (b - k0) : kb;
-        kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
+        if (kbi == KB && rpt <= 2) {  // panel rows fit in registers (<= 2 per thread)
+            if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+            else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+        } else {
+            kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
+        }
+        count_launches(1);
         const int nJ = b - kbi;
         if (nJ > 0) {
-            dim3 g((nJ + JT - 1) / JT, count);
-            ku<<<g, 256, usmem, s>>>(mats, b, k0, kbi, ws_piv);
+            if (b >= 128 && stash) {
+                constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
+                k_gj_gather<T><<<dim3((b + 63) / 64, count), 256, (2 * (size_t)b + kbi) * sizeof(int), s>>>(
+                    mats, b, k0, kbi, ws_piv, stash, slotmap);
+                count_launches(1);
+                const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
+                if (b % (16 / (int)sizeof(T)) == 0) {
+                    constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
+                    k_gj_update_vec<T, VV, BMU, BMU, 8, TNV><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                        mats, b, k0, kbi, stash, slotmap, tmu);
+                } else {
+                    k_gj_update_par<T, BMU, BMU, 8, TMU, TMU><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                        mats, b, k0, kbi, stash, slotmap, tmu);
+                }
+            } else {
+                dim3 g((nJ + JT - 1) / JT, count);
+                ku<<<g, 256, usmem, s>>>(mats, b, k0, kbi, ws_piv);
+            }
+            count_launches(1);
         }
     }
     dim3 gu((b + 255) / 256, count);
     k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
+    count_launches(1);
     cudaFreeAsync(amax, s);
+    if (stash) cudaFreeAsync(stash, s);
     return cudaGetLastError();
 }
 
@@ -438,16 +883,19 @@ cudaError_t gemm_simt(const GemmProb<T>* d_probs, int nprob, int b, cudaStream_t
         const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
         dim3 g(tm * tn, nprob);
         k_gemm_simt<T, BM, BN, 8, 4, 4><<<g, 256, 0, s>>>(d_probs, b, tm);
+        count_launches(1);
     } else if (b >= 128) {
         constexpr int BM = 128, BN = 128;
         const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
         dim3 g(tm * tn, nprob);
         k_gemm_simt<T, BM, BN, 8, 8, 8><<<g, 256, 0, s>>>(d_probs, b, tm);
+        count_launches(1);
     } else {
         constexpr int BM = 64, BN = 64;
         const int tm = (b + BM - 1) / BM, tn = (b + BN - 1) / BN;
         dim3 g(tm * tn, nprob);
         k_gemm_simt<T, BM, BN, 8, 4, 4><<<g, 256, 0, s>>>(d_probs, b, tm);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -478,7 +926,8 @@ k_sweep(const SweepProb<T>* __restrict__ probs, int b, int nrhs, int row_tiles) 
         T acc[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) acc[q] = T(0);
-        for (int t = 0; t < 3; ++t) {
+        const bool comb = P.sx[0] != nullptr;
+        for (int t = 0; t < (comb ? 1 : 3); ++t) {
             const T* __restrict__ Mt = P.m[t];
             if (Mt == nullptr) continue;
             const T* __restrict__ X = P.x[t];
@@ -495,7 +944,17 @@ k_sweep(const SweepProb<T>* __restrict__ probs, int b, int nrhs, int row_tiles) 
                 __syncthreads();
                 for (int i = tid; i < KC * NR; i += NT) {
                     const int c = i % KC, q = i / KC;
-                    xs[c][q] = (kc + c < b && q < nq) ? X[kc + c + (size_t)(q0 + q) * P.ldx] : T(0);
+                    T v = T(0);
+                    if (kc + c < b && q < nq) {
+                        const size_t o = kc + c + (size_t)(q0 + q) * P.ldx;
+                        if (comb) {
+                            v = P.sx[0][kc + c] * X[o];
+                            if (P.x[1]) v += P.sx[1][kc + c] * P.x[1][o];
+                        } else {
+                            v = X[o];
+                        }
+                    }
+                    xs[c][q] = v;
                 }
                 __syncthreads();
                 if (row < b) {
@@ -527,20 +986,187 @@ k_sweep(const SweepProb<T>* __restrict__ probs, int b, int nrhs, int row_tiles) 
     }
 }
 
+// Vectorized variant for blksz a multiple of V (16-byte loads of V rows):
+// thread (rg, g) owns rows row0 + V*rg .. +V-1 and the columns c = g mod KG;
+// the column loop is unrolled so that several 16-byte loads are in flight.
+
+// The multi-vector operand of each term is staged whole (b x NR) in dynamic
+// shared memory, so the column loop runs without barriers.
+template <class T, int V, int NR, int RG, int KG>
+__global__ void __launch_bounds__(RG * KG)
+k_sweep_vec(const SweepProb<T>* __restrict__ probs, int b, int nrhs, T* __restrict__ part) {
+    using VT = typename VecT<T, V>::type;
+    constexpr int NT = RG * KG, RT = RG * V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // split-K (part != NULL): CTA z covers columns [kbeg, kend) and writes raw
+    // partial sums part[((z * nprob + p) * b + row) * nrhs + q]
+    const int nsplit = gridDim.z, z = blockIdx.z;
+    const int KS = ((b + nsplit - 1) / nsplit + KG - 1) / KG * KG;
+    const int kbeg = z * KS, kend = (kbeg + KS) < b ? (kbeg + KS) : b;
+    const int kn = kend > kbeg ? kend - kbeg : 0;
+    T* xs = reinterpret_cast<T*>(smem_raw);            // [kn][NR]
+    T (*red)[RT][NR + 1] = reinterpret_cast<T (*)[RT][NR + 1]>(xs + (size_t)KS * NR);
+    const SweepProb<T> P = probs[blockIdx.y];
+    const int row0 = blockIdx.x * RT;
+    const int tid = threadIdx.x, rg = tid % RG, g = tid / RG;
+    const int row = row0 + rg * V;
+    const bool live = row < b;
+    const bool comb = P.sx[0] != nullptr;
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = (nrhs - q0) < NR ? (nrhs - q0) : NR;
+        T acc[V][NR];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[v][q] = T(0);
+        for (int t = 0; t < (comb ? 1 : 3); ++t) {
+            const T* __restrict__ Mt = P.m[t];
+            if (Mt == nullptr) continue;
+            const T* __restrict__ X = P.x[t];
+            if ((P.diag_mask >> t) & 1) {
+                if (g == 0 && live && z == 0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const T d = Mt[row + v];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+                            if (q < nq) acc[v][q] += d * X[row + v + (size_t)(q0 + q) * P.ldx];
+                    }
+                }
+                continue;
+            }
+            __syncthreads();
+            for (int i = tid; i < kn * NR; i += NT) {
+                const int cl = i % kn, q = i / kn, c = kbeg + cl;
+                T xv = T(0);
+                if (q < nq) {
+                    const size_t o = c + (size_t)(q0 + q) * P.ldx;
+                    if (comb) {
+                        xv = P.sx[0][c] * X[o];
+                        if (P.x[1]) xv += P.sx[1][c] * P.x[1][o];
+                    } else {
+                        xv = X[o];
+                    }
+                }
+                xs[cl * NR + q] = xv;
+            }
+            __syncthreads();
+            if (live) {
+                const T* mp = Mt + row + (size_t)kbeg * b;
+#pragma unroll 8
+                for (int c = g; c < kn; c += KG) {
+                    const VT mv = *reinterpret_cast<const VT*>(mp + (size_t)c * b);
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) {
+                        const T xq = xs[c * NR + q];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v][q] = fma(vget<VT, T>(mv, v), xq, acc[v][q]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) red[g][rg * V + v][q] = acc[v][q];
+        __syncthreads();
+        for (int i = tid; i < RT * NR; i += NT) {
+            const int r = i % RT, q = i / RT;
+            const int gr = row0 + r;
+            if (gr < b && q < nq) {
+                T sum = T(0);
+#pragma unroll
+                for (int gg = 0; gg < KG; ++gg) sum += red[gg][r][q];
+                if (part) {
+                    part[(((size_t)z * gridDim.y + blockIdx.y) * b + gr) * nrhs + q0 + q] = sum;
+                } else {
+                    T o = P.alpha * sum;
+                    if (P.cin) o += P.cin[gr + (size_t)(q0 + q) * P.ldc];
+                    P.out[gr + (size_t)(q0 + q) * P.ldo] = o;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// out = cin + alpha * sum_z part[z], fixed summation order.
+template <class T>
+__global__ void k_sweep_reduce(const SweepProb<T>* __restrict__ probs, int nprob, int b, int nrhs, int nsplit,
+                               const T* __restrict__ part) {
+    const long long total = (long long)nprob * b * nrhs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % nrhs);
+        const long long pr = t / nrhs;
+        const int row = (int)(pr % b), p = (int)(pr / b);
+        T sum = T(0);
+        for (int zz = 0; zz < nsplit; ++zz) sum += part[(((size_t)zz * nprob + p) * b + row) * nrhs + q];
+        const SweepProb<T>& P = probs[p];
+        T o = P.alpha * sum;
+        if (P.cin) o += P.cin[row + (size_t)q * P.ldc];
+        P.out[row + (size_t)q * P.ldo] = o;
+    }
+}
+
 template <class T>
 cudaError_t sweep_batched(const SweepProb<T>* d_probs, int nprob, int b, int nrhs, cudaStream_t s) {
     if (nprob <= 0 || nrhs <= 0) return cudaSuccess;
-    constexpr int RT = 64, KG = 4, KC = 64;
-    dim3 g((b + RT - 1) / RT, nprob);
+    constexpr int V = sizeof(T) == 8 ? 2 : 4;
+    constexpr int RG = 64, KG = 4, RT = RG * V;
+    const int NRv = nrhs == 1 ? 1 : (nrhs <= 4 ? 4 : 8);
+    const int rtiles = (b + RT - 1) / RT;
+    // few problems: split the columns over CTAs so that every SM streams
+    int nsplit = 1;
+    if ((long long)nprob * rtiles < 2 * 152) {
+        nsplit = (int)((4 * 152 + (long long)nprob * rtiles - 1) / ((long long)nprob * rtiles));
+        nsplit = std::min(nsplit, std::max(1, b / 64));
+    }
+    const int KS = ((b + nsplit - 1) / nsplit + KG - 1) / KG * KG;
+    const size_t vsm = ((size_t)KS * NRv + (size_t)KG * RT * (NRv + 1)) * sizeof(T);
+    if (b % V == 0 && b >= 64 && vsm <= 200 * 1024) {
+        T* part = nullptr;
+        if (nsplit > 1 &&
+            cudaMallocAsync(&part, sizeof(T) * (size_t)nsplit * nprob * b * nrhs, s) != cudaSuccess) {
+            cudaGetLastError();
+            return cudaErrorMemoryAllocation;
+        }
+        dim3 g(rtiles, nprob, nsplit);
+        if (NRv == 1) {
+            auto k = k_sweep_vec<T, V, 1, RG, KG>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
+        } else if (NRv == 4) {
+            auto k = k_sweep_vec<T, V, 4, RG, KG>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
+        } else {
+            auto k = k_sweep_vec<T, V, 8, RG, KG>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
+        }
+        count_launches(1);
+        if (part) {
+            const long long tot = (long long)nprob * b * nrhs;
+            int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
+            k_sweep_reduce<T><<<blocks, 256, 0, s>>>(d_probs, nprob, b, nrhs, nsplit, part);
+            count_launches(1);
+            cudaFreeAsync(part, s);
+        }
+        return cudaGetLastError();
+    }
+    constexpr int RT1 = 64, KG1 = 4, KC = 64;
+    dim3 g((b + RT1 - 1) / RT1, nprob);
     const int rt = g.x;
     if (nrhs == 1)
-        k_sweep<T, 1, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+        k_sweep<T, 1, RT1, KG1, KC><<<g, RT1 * KG1, 0, s>>>(d_probs, b, nrhs, rt);
     else if (nrhs <= 4)
-        k_sweep<T, 4, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+        k_sweep<T, 4, RT1, KG1, KC><<<g, RT1 * KG1, 0, s>>>(d_probs, b, nrhs, rt);
     else if (nrhs <= 8)
-        k_sweep<T, 8, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+        k_sweep<T, 8, RT1, KG1, KC><<<g, RT1 * KG1, 0, s>>>(d_probs, b, nrhs, rt);
     else
-        k_sweep<T, 16, RT, KG, KC><<<g, RT * KG, 0, s>>>(d_probs, b, nrhs, rt);
+        k_sweep<T, 16, RT1, KG1, KC><<<g, RT1 * KG1, 0, s>>>(d_probs, b, nrhs, rt);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -609,6 +1235,7 @@ cudaError_t stage_level0(int in_kind, int n, int b, const double* A, const doubl
         k_stage_dense<T><<<g, 256, 0, s>>>(n, b, A, D, C, dinv, dodd, aev, ak, cev, ck, bad);
     else
         k_stage_banded<T><<<g, 256, 0, s>>>(n, b, A, D, C, dinv, dodd, aev, ak, cev, ck, bad);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -631,7 +1258,7 @@ __global__ void k_resid_banded(int n, int b, const double* __restrict__ Dl, cons
         if (p + 1 < b) y += Du[(size_t)i * b + p] * xq[g + 1];
         if (i > 0) y += a[g] * xq[g - b];
         if (i + 1 < n) y += c[g] * xq[g + b];
-        r[t] = f[t] - y;
+        r[t] = f ? f[t] - y : y;  // f == NULL: plain product M x
     }
 }
 
@@ -643,6 +1270,7 @@ cudaError_t resid_banded(int n, int b, const double* Dl, const double* Dd, const
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
     k_resid_banded<<<(int)blocks, 256, 0, s>>>(n, b, Dl, Dd, Du, a, c, x, f, r, nrhs);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -690,7 +1318,9 @@ cudaError_t col_sumsq(const double* v, long long N, int nrhs, double* ws, double
     if (N < 1024 * 256) chunks = (int)((N + 255) / 256);
     if (chunks < 1) chunks = 1;
     k_sumsq_partial<<<dim3(chunks, nrhs), 256, 0, s>>>(v, N, ws);
+    count_launches(1);
     k_sumsq_final<<<nrhs, 256, 0, s>>>(ws, chunks, sumsq);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -714,16 +1344,105 @@ static int ew_blocks(long long n) {
 cudaError_t convert_d2f(const double* src, float* dst, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_d2f<<<ew_blocks(n), 256, 0, s>>>(src, dst, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t add_f2d(double* x, const float* d, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_add_f2d<<<ew_blocks(n), 256, 0, s>>>(x, d, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t add_d2d(double* x, const double* d, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_add_d2d<<<ew_blocks(n), 256, 0, s>>>(x, d, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+cudaError_t convert_f2d(const float* src, double* dst, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_f2d<<<ew_blocks(n), 256, 0, s>>>(src, dst, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// grid (chunks, nrhs, nvec); ws[(i * nrhs + q) * chunks + c]
+__global__ void k_multi_dot_partial(const double* __restrict__ V, const double* __restrict__ w, long long N,
+                                    int nrhs, double* __restrict__ ws) {
+    __shared__ double red[32];
+    const int q = blockIdx.y, i = blockIdx.z, chunks = gridDim.x;
+    const long long chunk = (N + chunks - 1) / chunks;
+    const long long lo = blockIdx.x * chunk;
+    long long hi = lo + chunk;
+    if (hi > N) hi = N;
+    const double* vq = V + ((long long)i * nrhs + q) * N;
+    const double* wq = w + (long long)q * N;
+    double s = 0.0;
+    for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) s += vq[r] * wq[r];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) ws[((long long)i * nrhs + q) * chunks + blockIdx.x] = s;
+    }
+}
+
+static int dot_chunks(long long N) {
+    int chunks = 256;
+    if (N < 256LL * 1024) chunks = (int)((N + 1023) / 1024);
+    return chunks < 1 ? 1 : chunks;
+}
+
+cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws, double* out,
+                      cudaStream_t s) {
+    if (nvec <= 0 || nrhs <= 0) return cudaSuccess;
+    const int chunks = dot_chunks(N);
+    k_multi_dot_partial<<<dim3(chunks, nrhs, nvec), 256, 0, s>>>(V, w, N, nrhs, ws);
+    count_launches(1);
+    k_sumsq_final<<<nvec * nrhs, 256, 0, s>>>(ws, chunks, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_multi_axpy(double* __restrict__ w, const double* __restrict__ V, int nvec,
+                             const double* __restrict__ coef, long long N, int nrhs) {
+    const long long total = N * nrhs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t / N);
+        double acc = w[t];
+        for (int i = 0; i < nvec; ++i) acc += coef[i * nrhs + q] * V[(long long)i * total + t];
+        w[t] = acc;
+    }
+}
+
+cudaError_t multi_axpy(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
+                       cudaStream_t s) {
+    if (nvec <= 0 || nrhs <= 0) return cudaSuccess;
+    k_multi_axpy<<<ew_blocks(N * nrhs), 256, 0, s>>>(w, V, nvec, coef, N, nrhs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_col_scale(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ sc,
+                            long long N, int nrhs) {
+    const long long total = N * nrhs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        v[t] = w[t] * sc[t / N];
+}
+
+cudaError_t col_scale(double* v, const double* w, const double* scale, long long N, int nrhs, cudaStream_t s) {
+    if (nrhs <= 0) return cudaSuccess;
+    k_col_scale<<<ew_blocks(N * nrhs), 256, 0, s>>>(v, w, scale, N, nrhs);
+    count_launches(1);
     return cudaGetLastError();
 }
 

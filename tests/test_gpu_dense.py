@@ -193,6 +193,31 @@ def test_refinement_not_converged_reported(lib):
         lib.acr_free(h)
 
 
+@pytest.mark.parametrize("refine", [0, 1])
+def test_refinement_methods_poisson(lib, refine):
+    """FGMRES and classic refinement both reach 1e-8 on an SPD problem."""
+    P = syn.make_config(0, 128)
+    F = syn.rhs_uniform(P.N, 3, 2000)
+    h = factor_banded(lib, P, prec=2, refine=refine)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all() and 1 <= it <= 10
+
+
+def test_refinement_off_reports_not_converged(lib):
+    P = syn.make_config(0, 128)
+    F = syn.rhs_uniform(P.N, 2, 2000)
+    h = factor_banded(lib, P, prec=2, refine=2)
+    try:
+        with pytest.raises(lib.AcrError) as ei:
+            solve(lib, h, F)
+        assert ei.value.code == lib.ACR_ERR_NOT_CONVERGED and ei.value.iters == 1
+    finally:
+        lib.acr_free(h)
+
+
 def test_stats(lib):
     P = syn.make_config(0, 32)
     h = factor_banded(lib, P)
@@ -200,7 +225,12 @@ def test_stats(lib):
         s = lib.acr_stats(h)
         assert s["levels"] == 6 and s["nblk"] == 32 and s["blksz"] == 32
         assert s["factor_ms"] > 0 and s["factor_flops"] > 0
-        assert s["factor_bytes"] == lib.acr_factor_bytes(32, 32, 0.0) - 3 * 32 * 32 * 32 * 8
+        # structured level 0 keeps diagonals only: below the dense-storage bound
+        o = lib.acr_default_opts()
+        o.input_kind = lib.ACR_BANDED
+        bound = lib.acr_factor_bytes(32, 32, 0.0, o) - 5 * 32 * 32 * 8
+        assert 0 < s["factor_bytes"] < bound
+        assert s["launches_factor"] > 0
     finally:
         lib.acr_free(h)
 
@@ -221,10 +251,14 @@ def test_full_size_convdiff_512(lib, prec):
 
 
 def test_full_size_helmholtz_1m(lib):
-    """The N = 1048576 Helmholtz workload: mixed precision + refinement."""
+    """The N = 1048576 Helmholtz workload: mixed precision + FGMRES refinement
+    (the launch configuration the benchmark times).  Block cyclic reduction of
+    this indefinite operator amplifies rounding (near-singular reduced
+    blocks), so plain refinement diverges and FGMRES needs a few dozen
+    preconditioner solves."""
     P = syn.make_config(3)
     F = syn.rhs_uniform(P.N, 8, 2003)
-    h = factor_banded(lib, P, prec=2)
+    h = factor_banded(lib, P, prec=2, ir_max_iter=60)
     try:
         X, res, it = solve(lib, h, F)
     finally:
