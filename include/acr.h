@@ -165,6 +165,36 @@ int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts *o, size_t 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *acr_last_error(void);
 
+/* ---- batched block inversion without device allocation -------------------
+ * The paper has no counterpart to this call: it is a service for callers that
+ * cannot allocate device memory when they need it -- code running inside
+ * another framework's memory pool that has reserved nearly all of the GPU,
+ * latency-critical paths that cannot absorb an allocation, its failure or the
+ * device synchronisation that freeing can cause.
+ *
+ * Inverts, in place, `count` blocks of blksz x blksz (column-major, block
+ * stride blksz*blksz) with the same partial-pivoting Gauss-Jordan kernels as
+ * the factorization, in FP64.  mats and info are device memory owned by the
+ * caller; info receives per block 0, or k+1 if pivot k was zero or not finite
+ * (that block's contents are then meaningless).
+ *
+ * Every temporary lives in one fixed scratch array of
+ * ACR_NOALLOC_SCRATCH_BYTES compiled into the library, which each GPU that
+ * loads the library holds until the process exits; the call allocates and
+ * frees nothing.  A batch whose temporaries exceed that size returns
+ * ACR_ERR_INVALID_ARG (split the batch); blocks up to blksz 159 need no
+ * scratch at all.
+ *
+ * The work is queued on `stream` (a cudaStream_t, NULL for the legacy
+ * default stream) and the call returns without waiting for it.  All calls
+ * share the one scratch array per device, so calls whose work can overlap on
+ * the GPU (different streams, or host threads racing) corrupt each other:
+ * order them on one stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call outside any stream capture. */
+#define ACR_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int acr_block_inverse_noalloc(int blksz, int count, double *mats, int *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

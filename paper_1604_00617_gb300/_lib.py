@@ -44,7 +44,10 @@ _NAMES = {0: "ACR_OK", -1: "ACR_ERR_INVALID_ARG", -2: "ACR_ERR_OOM", -3: "ACR_ER
 
 # every symbol include/acr.h declares
 EXPORTED = ["acr_default_opts", "acr_factor", "acr_factor_ex", "acr_solve", "acr_solve_ex",
-            "acr_free", "acr_stats", "acr_factor_bytes", "acr_last_error"]
+            "acr_free", "acr_stats", "acr_factor_bytes", "acr_last_error", "acr_block_inverse_noalloc"]
+
+# fixed scratch of acr_block_inverse_noalloc (ACR_NOALLOC_SCRATCH_BYTES)
+ACR_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class AcrError(RuntimeError):
@@ -104,6 +107,8 @@ def load(path: str = LIB_PATH):
     lib.acr_factor_bytes.restype = i
     lib.acr_last_error.argtypes = []
     lib.acr_last_error.restype = ctypes.c_char_p
+    lib.acr_block_inverse_noalloc.argtypes = [i, i, vp, vp, vp]
+    lib.acr_block_inverse_noalloc.restype = i
     return lib
 
 
@@ -216,3 +221,19 @@ def acr_factor_bytes(nblk: int, blksz: int, tol: float = 0.0, opts: acr_opts | N
     out = ctypes.c_size_t(0)
     _check(_lib.acr_factor_bytes(nblk, blksz, float(tol), ctypes.byref(o), ctypes.byref(out)))
     return out.value
+
+
+def acr_block_inverse_noalloc(blksz: int, count: int, mats, info, stream=None) -> None:
+    """``acr_block_inverse_noalloc``: invert ``count`` column-major blocks in
+    place on the device without allocating (``mats``: float64 device tensor,
+    ``info``: int32 device tensor of ``count``).  Queued on ``stream`` (a CUDA
+    stream handle or None); returns without waiting."""
+    if hasattr(info, "data_ptr"):
+        import torch
+        if info.dtype != torch.int32 or info.numel() < count:
+            raise TypeError("info must be an int32 tensor with count elements")
+        iptr = ctypes.c_void_p(info.data_ptr())
+    else:
+        raise TypeError("info must be a device tensor")
+    _check(_lib.acr_block_inverse_noalloc(int(blksz), int(count), _ptr(mats, blksz * blksz * count), iptr,
+                                          ctypes.c_void_p(stream) if stream else None))

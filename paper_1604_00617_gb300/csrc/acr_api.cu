@@ -40,8 +40,15 @@
 using namespace acr;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+int acr::set_last_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+
+namespace {
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];

@@ -75,6 +75,18 @@ cudaError_t stage_diagonals(const double* a, const double* c, int n, int b, T* a
 template <class T>
 cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaStream_t s);
 
+// Same inversion with every temporary in caller-provided scratch (no device
+// allocation); gj_scratch_bytes gives the bytes it needs (0 when the blocks
+// fit the shared-memory kernel).  Returns cudaErrorInvalidValue if the
+// scratch is too small.
+template <class T>
+size_t gj_scratch_bytes(int b, int count);
+template <class T>
+cudaError_t gj_inverse_scratch(T* mats, int b, int count, int* info, void* scratch, size_t scratch_bytes,
+                               cudaStream_t s);
+// Record a message for acr_last_error() on this thread; returns code.
+int set_last_error(int code, const char* msg);
+
 // --- batched multi-term block product ---------------------------------------
 template <class T>
 cudaError_t gemm_batched(const GemmProb<T>* d_probs, int nprob, int b, int use_tc, cudaStream_t s);

@@ -806,6 +806,90 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
     return cudaGetLastError();
 }
 
+// Scratch layout of gj_inverse_scratch (each part 256-byte aligned):
+// pivots (count*b ints), max|entry| (count T), row stash (count*2*kb*b T),
+// slot map (count*b ints).  The shared-memory path needs none.
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class T>
+size_t gj_scratch_bytes(int b, int count) {
+    if (count <= 0 || gj_small_smem<T>(b) <= 200 * 1024) return 0;
+    const int kb = sizeof(T) == 8 ? 16 : 32;
+    return al256(sizeof(int) * (size_t)count * b) + al256(sizeof(T) * (size_t)count) +
+           al256(sizeof(T) * (size_t)count * 2 * kb * b) + al256(sizeof(int) * (size_t)count * b);
+}
+
+// The same batched inversion as gj_inverse, with every temporary taken from
+// the caller's scratch (no device allocation).  Kernels and launch sequence
+// are those of gj_inverse's blocked path.
+template <class T>
+cudaError_t gj_inverse_scratch(T* mats, int b, int count, int* info, void* scratch, size_t scratch_bytes,
+                               cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (scratch_bytes < gj_scratch_bytes<T>(b, count)) return cudaErrorInvalidValue;
+    cudaMemsetAsync(info, 0, sizeof(int) * count, s);
+    const size_t small = gj_small_smem<T>(b);
+    if (small <= 200 * 1024) {
+        auto kern = k_gj_small<T, 256>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
+        kern<<<count, 256, small, s>>>(mats, b, info);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    constexpr int KB = sizeof(T) == 8 ? 16 : 32;
+    const int kb = KB;
+    char* p = static_cast<char*>(scratch);
+    int* ws_piv = reinterpret_cast<int*>(p);
+    p += al256(sizeof(int) * (size_t)count * b);
+    T* amax = reinterpret_cast<T*>(p);
+    p += al256(sizeof(T) * (size_t)count);
+    T* stash = reinterpret_cast<T*>(p);
+    p += al256(sizeof(T) * (size_t)count * 2 * kb * b);
+    int* slotmap = reinterpret_cast<int*>(p);
+    cudaMemsetAsync(amax, 0, sizeof(T) * count, s);  // the max reduction accumulates into zeros
+    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
+    count_launches(1);
+    constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
+    const size_t psmem = (size_t)b * kb * sizeof(T);
+    auto kp = k_gj_panel<T, 512>;
+    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    const int rpt = (b + 511) / 512;
+    for (int k0 = 0; k0 < b; k0 += kb) {
+        const int kbi = (b - k0) < kb ? (b - k0) : kb;
+        if (kbi == KB && rpt <= 2) {
+            if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+            else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+        } else {
+            kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
+        }
+        count_launches(1);
+        const int nJ = b - kbi;
+        if (nJ > 0) {
+            k_gj_gather<T><<<dim3((b + 63) / 64, count), 256, (2 * (size_t)b + kbi) * sizeof(int), s>>>(
+                mats, b, k0, kbi, ws_piv, stash, slotmap);
+            count_launches(1);
+            const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
+            if (b % (16 / (int)sizeof(T)) == 0) {
+                constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
+                k_gj_update_vec<T, VV, BMU, BMU, 8, TNV><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                    mats, b, k0, kbi, stash, slotmap, tmu);
+            } else {
+                k_gj_update_par<T, BMU, BMU, 8, TMU, TMU><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                    mats, b, k0, kbi, stash, slotmap, tmu);
+            }
+            count_launches(1);
+        }
+    }
+    dim3 gu((b + 255) / 256, count);
+    k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template size_t gj_scratch_bytes<double>(int, int);
+template size_t gj_scratch_bytes<float>(int, int);
+template cudaError_t gj_inverse_scratch<double>(double*, int, int, int*, void*, size_t, cudaStream_t);
+template cudaError_t gj_inverse_scratch<float>(float*, int, int, int*, void*, size_t, cudaStream_t);
+
 // ===========================================================================
 // Batched multi-term block product on CUDA cores (SIMT).
 // CTA tile BM x BN, K step BK, thread tile TM x TN (rows interleaved so that
