@@ -33,7 +33,7 @@ ACR_DENSE = 0
 ACR_BANDED = 1
 
 # tensor-core block products compiled into this build
-TC_BUILT = False
+TC_BUILT = True
 
 ACR_REFINE_FGMRES = 0
 ACR_REFINE_IR = 1

@@ -355,6 +355,77 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         CK(cudaMemcpyAsync(dprobs.p, probs.data(), probs.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice, s));
     const GemmProb<T>* dp = dprobs.as<GemmProb<T>>();
 
+    // ---- tensor-core tables: one tensor map per level array, same problems ----
+    bool tc = false;
+    DevBuf dmaps, dtc, dterr;
+    std::vector<size_t> tc1_off(T_ + 1), tc1_cnt(T_ + 1), tc2_off(T_ + 1), tc2_cnt(T_ + 1);
+    if constexpr (sizeof(T) == 4) {
+        if (h->prec == ACR_FP32TC_IR && tc_supported(b)) {
+            tc = true;
+            const size_t mb = tc_map_bytes();
+            std::vector<unsigned char> maps;
+            auto add_map = [&](const T* base, int count, int role) -> int {
+                const size_t at = maps.size();
+                maps.resize(at + mb);
+                if (tc_encode_map(maps.data() + at, reinterpret_cast<const float*>(base), b, count, role) != 0)
+                    return -1;
+                return (int)(at / mb);
+            };
+            std::vector<TcProb> tp;
+            for (int t = (b0 ? 1 : 0); t < T_; ++t) {
+                const Level& L = h->lev[t];
+                const Level& Ln = h->lev[t + 1];
+                const int mDinv = add_map(h->P<T>(L.off_dinv), L.ne, 0), mAev = add_map(t_aev(t), L.ne, 1),
+                          mCev = add_map(t_cev(t), L.ne, 1), mAk = add_map(h->P<T>(L.off_ak), L.nk, 0),
+                          mCk = add_map(h->P<T>(L.off_ck), L.nk, 0), mXa = add_map(h->P<T>(L.off_xa), L.ne, 1),
+                          mXc = add_map(h->P<T>(L.off_xc), L.ne, 1);
+                if (std::min({mDinv, mAev, mCev, mAk, mCk, mXa, mXc}) < 0)
+                    return fail(ACR_ERR_CUDA, "tensor map encoding failed (level %d)", t);
+                auto mk1 = [&](T* out, const T* cin, float al, float be, int am, int az, int bm, int bz) {
+                    TcProb q;
+                    memset(&q, 0, sizeof(q));
+                    q.out = reinterpret_cast<float*>(out);
+                    q.cin = reinterpret_cast<const float*>(cin);
+                    q.alpha = al; q.beta = be; q.nterm = 1;
+                    q.amap[0] = am; q.az[0] = az; q.bmap[0] = bm; q.bz[0] = bz;
+                    return q;
+                };
+                tc1_off[t] = tp.size();
+                for (int e = 0; e < L.ne; ++e) {
+                    const int j = 2 * e;
+                    if (j > 0) tp.push_back(mk1(h->P<T>(L.off_xa) + e * bb, nullptr, 1.f, 0.f, mDinv, e, mAev, e));
+                    if (j + 1 < L.m) tp.push_back(mk1(h->P<T>(L.off_xc) + e * bb, nullptr, 1.f, 0.f, mDinv, e, mCev, e));
+                }
+                tc1_cnt[t] = tp.size() - tc1_off[t];
+                tc2_off[t] = tp.size();
+                for (int k = 0; k < L.nk; ++k) {
+                    const int i = 2 * k + 1;
+                    const bool kev = (k % 2) == 0;
+                    const int ks = k / 2;
+                    TcProb pd = mk1(kev ? h->P<T>(Ln.off_dinv) + ks * bb : t_dodd(t + 1) + ks * bb,
+                                    t_dodd(t) + k * bb, -1.f, 1.f, mAk, k, mXc, k);
+                    if (i + 1 < L.m) { pd.nterm = 2; pd.amap[1] = mCk; pd.az[1] = k; pd.bmap[1] = mXa; pd.bz[1] = k + 1; }
+                    tp.push_back(pd);
+                    if (i >= 3)
+                        tp.push_back(mk1(kev ? t_aev(t + 1) + ks * bb : h->P<T>(Ln.off_ak) + ks * bb, nullptr, -1.f, 0.f,
+                                         mAk, k, mXa, k));
+                    if (i + 2 < L.m)
+                        tp.push_back(mk1(kev ? t_cev(t + 1) + ks * bb : h->P<T>(Ln.off_ck) + ks * bb, nullptr, -1.f, 0.f,
+                                         mCk, k, mXc, k + 1));
+                }
+                tc2_cnt[t] = tp.size() - tc2_off[t];
+            }
+            CK(dmaps.alloc(std::max<size_t>(maps.size(), 128), s));
+            if (!maps.empty()) CK(cudaMemcpyAsync(dmaps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice, s));
+            CK(dtc.alloc(std::max<size_t>(1, tp.size()) * sizeof(TcProb), s));
+            if (!tp.empty()) CK(cudaMemcpyAsync(dtc.p, tp.data(), tp.size() * sizeof(TcProb), cudaMemcpyHostToDevice, s));
+            CK(dterr.alloc(sizeof(int), s));
+            CK(cudaMemsetAsync(dterr.p, 0, sizeof(int), s));
+            // the host tables must outlive the asynchronous uploads
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -412,8 +483,14 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         }
         c0 = launch_count();
         CK(mark(1));
-        CK(gemm_batched<T>(dp + g1_off[t], (int)g1_cnt[t], b, use_tc, s));
-        CK(gemm_batched<T>(dp + g2_off[t], (int)g2_cnt[t], b, use_tc, s));
+        if (tc) {
+            const TcProb* tq = dtc.as<TcProb>();
+            CK(gemm_tc(tq + tc1_off[t], (int)tc1_cnt[t], dmaps.p, b, dterr.as<int>(), s));
+            CK(gemm_tc(tq + tc2_off[t], (int)tc2_cnt[t], dmaps.p, b, dterr.as<int>(), s));
+        } else {
+            CK(gemm_batched<T>(dp + g1_off[t], (int)g1_cnt[t], b, use_tc, s));
+            CK(gemm_batched<T>(dp + g2_off[t], (int)g2_cnt[t], b, use_tc, s));
+        }
         CK(mark(1));
         gemm_l += launch_count() - c0;
     }
@@ -425,6 +502,11 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (tc) {
+        int terr = 0;
+        CK(cudaMemcpy(&terr, dterr.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (terr) return fail(ACR_ERR_TIMEOUT, "tensor-core product kernel gave up on a bounded pipeline wait");
+    }
     if (info[ninfo]) return fail(ACR_ERR_INVALID_ARG, "input holds a NaN or Inf");
     for (int t = 0; t <= T_; ++t)
         for (int e = 0; e < h->lev[t].ne; ++e)
@@ -987,7 +1069,6 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     if (op.ir_max_iter <= 0) op.ir_max_iter = 20;
     if (!(op.ir_tol > 0)) op.ir_tol = 1e-8;
     if (tol > 0) return fail(ACR_ERR_INVALID_ARG, "compressed (HODLR) blocks: tol > 0 not available in this build");
-    if (op.precision == ACR_FP32TC_IR) return fail(ACR_ERR_INVALID_ARG, "tensor-core products not available in this build");
     acr_ctx* h = new (std::nothrow) acr_ctx();
     if (!h) return fail(ACR_ERR_OOM, "host allocation failed");
     h->n = nblk; h->b = blksz; h->prec = op.precision; h->in_kind = op.input_kind; h->tol = tol; h->opts = op;

@@ -91,6 +91,25 @@ int set_last_error(int code, const char* msg);
 template <class T>
 cudaError_t gemm_batched(const GemmProb<T>* d_probs, int nprob, int b, int use_tc, cudaStream_t s);
 
+// --- tensor-core block products (tcgen05, three-term TF32 split) ------------
+// One problem: out = beta * cin + alpha * sum_t A_t B_t with A_t block az[t]
+// of the array described by tensor map amap[t] (left-operand map) and B_t
+// block bz[t] of map bmap[t] (right-operand map).  blksz a multiple of 128.
+struct TcProb {
+    float* out;
+    const float* cin;
+    float alpha, beta;
+    int nterm;
+    int amap[2], az[2], bmap[2], bz[2];
+};
+bool tc_supported(int b);
+size_t tc_map_bytes();
+// Encode the tensor map of `count` contiguous b x b column-major FP32 blocks
+// starting at base, as left (role 0) or right (role 1) operand.  0 on success.
+int tc_encode_map(void* map_out, const float* base, int b, int count, int role);
+// d_err: set to 1 if a CTA gave up on a bounded wait (then later CTAs skip).
+cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s);
+
 // --- batched block x multi-vector (solve sweeps, dense FP64 residual) ----
 template <class T>
 cudaError_t sweep_batched(const SweepProb<T>* d_probs, int nprob, int b, int nrhs, cudaStream_t s);

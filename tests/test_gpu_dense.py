@@ -266,3 +266,58 @@ def test_full_size_helmholtz_1m(lib):
     assert (res <= 1e-8).all(), res
     r = np.linalg.norm(F - P.matvec(X), axis=0) / np.linalg.norm(F, axis=0)
     assert (r <= 1.5e-8).all(), r
+
+
+@pytest.mark.parametrize("n,b", [(2, 128), (3, 128), (5, 256), (4, 384), (9, 128)])
+def test_tensor_core_products_match_simt(lib, n, b):
+    """tcgen05 three-term TF32 products agree with the FP32 CUDA-core products
+    to FP32 rounding (one sweep, no refinement), and refine to the oracle."""
+    A, D, C = syn.random_blocks(n, b, seed=n + b)
+    F = np.random.default_rng(n).uniform(-1, 1, (n * b, 3))
+    X = {}
+    for prec in (1, 2):
+        h = factor(lib, A, D, C, prec=prec, refine=2, ir_tol=1.0)
+        try:
+            X[prec], _, _ = solve(lib, h, F)
+        finally:
+            lib.acr_free(h)
+    assert relerr(X[1], X[2]) <= 1e-6
+    h = factor(lib, A, D, C, prec=1)
+    try:
+        Xr, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all()
+    assert relerr(Xr, oracle.bcr_solve(A, D, C, F)) <= 1e-9
+
+
+@pytest.mark.parametrize("idx,n", [(1, 128), (2, 256), (3, 256)])
+def test_pde_tensor_core_refinement(lib, idx, n):
+    P = syn.make_config(idx, n)
+    A, D, C = P.dense_blocks()
+    F = syn.rhs_uniform(P.N, 4, 2000 + idx)
+    h = factor_banded(lib, P, prec=1, ir_max_iter=60)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all(), (res, it)
+    r = np.linalg.norm(F - P.matvec(X), axis=0) / np.linalg.norm(F, axis=0)
+    assert (r <= 1.5e-8).all()
+    if n <= 128:
+        assert relerr(X, oracle.bcr_solve(A, D, C, F)) <= 1e-6
+
+
+def test_full_size_helmholtz_1m_tensor_cores(lib):
+    """The benchmark's launch configuration: N = 1048576 Helmholtz, FP32 factor
+    with tcgen05 products, FGMRES to 1e-8."""
+    P = syn.make_config(3)
+    F = syn.rhs_uniform(P.N, 8, 2003)
+    h = factor_banded(lib, P, prec=1, ir_max_iter=60)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all(), res
+    r = np.linalg.norm(F - P.matvec(X), axis=0) / np.linalg.norm(F, axis=0)
+    assert (r <= 1.5e-8).all(), r
