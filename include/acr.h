@@ -90,8 +90,10 @@ typedef struct {
     int refine;         /* enum acr_refine, default ACR_REFINE_FGMRES */
 } acr_opts;
 
+#define ACR_FGMRES_RESTART 50
+
 enum acr_refine {
-    /* restarted FGMRES(30) in FP64, right-preconditioned by the factor's
+    /* restarted FGMRES(ACR_FGMRES_RESTART) in FP64, right-preconditioned by the factor's
      * sweeps (converges where plain refinement diverges, e.g. indefinite
      * Helmholtz, whose reduced blocks amplify rounding errors) */
     ACR_REFINE_FGMRES = 0,

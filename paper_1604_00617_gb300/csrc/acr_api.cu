@@ -856,7 +856,7 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
         }
     } else {
         // restarted FGMRES(m), right preconditioned, one Krylov space per column
-        const int m = std::min(30, maxit);
+        const int m = std::min(ACR_FGMRES_RESTART, maxit);
         DevBuf V, Z;
         CK(V.alloc((size_t)(m + 1) * NQ * 8, s));
         CK(Z.alloc((size_t)m * NQ * 8, s));

@@ -3,8 +3,8 @@
 // The Schur complement products of Eq. "fund" (D_j^-1 A_j, D_j^-1 C_j and
 // D_i - A_i XC_{i-1} - C_i XA_{i+1}, ...) are dense b x b contractions.  This
 // kernel runs them with tcgen05.mma (kind::tf32, FP32 accumulation in TMEM)
-// at FP32 accuracy by the three-term split  x = hi + lo,  hi = x with the low
-// 13 mantissa bits cleared (exact in TF32),  lo = x - hi (exact in FP32):
+// at FP32 accuracy by the three-term split  x ~= hi + lo,  hi = x rounded to
+// the nearest TF32 value,  lo = (x - hi) rounded to the nearest TF32 value:
 //     A B  ~=  Ahi Bhi + Ahi Blo + Alo Bhi       (the Alo Blo term is ~2^-22).
 //
 // One CTA computes one 128 x 128 tile of one problem:
@@ -103,7 +103,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+// Round to the nearest TF32 value (ties away from zero): add half a TF32 ulp
+// to the magnitude bits, then clear the 13 low mantissa bits.  Both parts of
+// the split are rounded this way, so the MMA sees exactly representable
+// operands and the split error (<= 2^-23 |x|) has no bias that could grow
+// along the 1024-long contractions.
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+__device__ __forceinline__ float tf32_hi(float x) { return tf32_rn(x); }
 
 // byte offset of element (row, k) in a 128-row x 32-k K-major SW128 tile
 __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
@@ -211,10 +219,10 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
             for (int c = 0; c < BK / 4; ++c) {
                 float4 h, l;
                 float x;
-                x = araw[(4 * c + 0) * BM + t]; h.x = tf32_hi(x); l.x = x - h.x;
-                x = araw[(4 * c + 1) * BM + t]; h.y = tf32_hi(x); l.y = x - h.y;
-                x = araw[(4 * c + 2) * BM + t]; h.z = tf32_hi(x); l.z = x - h.z;
-                x = araw[(4 * c + 3) * BM + t]; h.w = tf32_hi(x); l.w = x - h.w;
+                x = araw[(4 * c + 0) * BM + t]; h.x = tf32_hi(x); l.x = tf32_rn(x - h.x);
+                x = araw[(4 * c + 1) * BM + t]; h.y = tf32_hi(x); l.y = tf32_rn(x - h.y);
+                x = araw[(4 * c + 2) * BM + t]; h.z = tf32_hi(x); l.z = tf32_rn(x - h.z);
+                x = araw[(4 * c + 3) * BM + t]; h.w = tf32_hi(x); l.w = tf32_rn(x - h.w);
                 const uint32_t o = sw128_off(t, 4 * c);
                 *reinterpret_cast<float4*>(ahi + o) = h;
                 *reinterpret_cast<float4*>(alo + o) = l;
@@ -225,10 +233,10 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
                 const int i = t + j * 128;
                 const float4 v = bt[i];
                 float4 h, l;
-                h.x = tf32_hi(v.x); l.x = v.x - h.x;
-                h.y = tf32_hi(v.y); l.y = v.y - h.y;
-                h.z = tf32_hi(v.z); l.z = v.z - h.z;
-                h.w = tf32_hi(v.w); l.w = v.w - h.w;
+                h.x = tf32_hi(v.x); l.x = tf32_rn(v.x - h.x);
+                h.y = tf32_hi(v.y); l.y = tf32_rn(v.y - h.y);
+                h.z = tf32_hi(v.z); l.z = tf32_rn(v.z - h.z);
+                h.w = tf32_hi(v.w); l.w = tf32_rn(v.w - h.w);
                 bt[i] = h;
                 blo[i] = l;
             }
