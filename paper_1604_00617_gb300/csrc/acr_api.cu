@@ -132,6 +132,17 @@ struct acr_ctx {
     std::vector<Level> lev;
     DevBuf arena;   // persistent factors
     DevBuf op;      // FP64 copy of the original operator (refinement / residual)
+    // compressed (HODLR) storage, tol > 0: the dense arena is released
+    bool compressed = false;
+    int leaf = 0, hL = 0;
+    double tol_eff = 0.0;
+    DevBuf hpool;    // leaves of every block, then the node data of every block
+    DevBuf hnodes;   // HNode table
+    DevBuf hblks;    // HBlk table
+    DevBuf hdiag;    // level-0 diagonals (a, c of eliminated and kept blocks) when band0
+    std::vector<std::vector<std::vector<int>>> bid;  // [level][array][slot] -> block id, -1 if unused
+    size_t hd_off[4] = {0, 0, 0, 0};                 // element offsets of the 4 diagonal arrays in hdiag
+    std::vector<double> hblk_bytes;                  // compressed bytes of every block
     std::mutex mu;
     acr_stats_t st{};
     ~acr_ctx() {
@@ -211,6 +222,239 @@ double factor_flops(const std::vector<Level>& lev, int b, size_t t0 = 0) {
         }
     }
     return f;
+}
+
+// ---------------------------------------------------------------------------
+// HODLR recompression of every stored factor block (tol > 0).  The blocks are
+// formed densely by the reduction; each one is then held as a HODLR matrix:
+// dense leaves plus off-diagonal U V^T with ranks truncated at
+// sigma_k > tol * sigma_1 of each node (randomized sketch, Householder QR,
+// Jacobi SVD; nodes the sketch cannot certify stay dense).  The dense arena
+// is released afterwards; the sweeps then read the compressed blocks.
+// ---------------------------------------------------------------------------
+int default_leaf(int b) {
+    if (b >= 512) return 64;
+    if (b >= 256) return 32;
+    return std::min(b, 16);
+}
+
+template <class T>
+int compress_factor(acr_ctx* h) {
+    const int b = h->b;
+    const size_t bb = h->bb();
+    cudaStream_t s = h->stream;
+    // tree depth: the largest L with b divisible by 2^L and leaves b / 2^L no
+    // smaller than the requested leaf size
+    const int want = std::max(1, h->opts.leaf > 0 ? h->opts.leaf : default_leaf(b));
+    int L = 0;
+    while ((b % (2 << L)) == 0 && (b >> (L + 1)) >= want) ++L;
+    const int leaf = b >> L;
+    h->leaf = leaf;
+    h->hL = L;
+    const int max_rank = h->opts.max_rank > 0 ? h->opts.max_rank : 0;
+    const int kmax = max_rank > 0 ? std::min(64, std::max(16, ((max_rank + 8) + 1) / 2 * 2)) : 32;
+    const double tol = h->tol_eff;
+    const int T_ = h->levels() - 1;
+
+    // ---- the stored blocks -----------------------------------------------------
+    std::vector<const T*> blocks;
+    h->bid.assign(T_ + 1, std::vector<std::vector<int>>(5));
+    for (int t = 0; t <= T_; ++t) {
+        const Level& Lv = h->lev[t];
+        const bool diag0 = h->band0 && t == 0;
+        auto add = [&](int arr, size_t off, int count, auto used) {
+            h->bid[t][arr].assign(count, -1);
+            for (int e = 0; e < count; ++e)
+                if (used(e)) {
+                    h->bid[t][arr][e] = (int)blocks.size();
+                    blocks.push_back(h->P<T>(off) + (size_t)e * bb);
+                }
+        };
+        add(0, Lv.off_dinv, Lv.ne, [](int) { return true; });
+        if (t == T_ || diag0) continue;
+        add(1, Lv.off_xa, Lv.ne, [](int e) { return 2 * e > 0; });
+        add(2, Lv.off_xc, Lv.ne, [&](int e) { return 2 * e + 1 < Lv.m; });
+        add(3, Lv.off_ak, Lv.nk, [](int) { return true; });
+        add(4, Lv.off_ck, Lv.nk, [&](int k) { return 2 * k + 2 < Lv.m; });
+    }
+    const int NB = (int)blocks.size();
+    const int npb = (1 << (L + 1)) - 2;  // off-diagonal nodes per block
+
+    // ---- sketch, QR + SVD, V for every tree level ------------------------------
+    const int omr = std::max(1, b / 2);
+    DevBuf om;
+    CK(om.alloc((size_t)omr * kmax * sizeof(T), s));
+    CK(hodlr_omega<T>(om.as<T>(), (long long)omr * kmax, 0x5eedacc0ull + (uint64_t)b, s));
+    std::vector<DevBuf> Uk(L + 1), Vk(L + 1), Sg(L + 1);
+    std::vector<int> kl(L + 1, 0);
+    std::vector<std::vector<T>> hsig(L + 1);
+    for (int l = 1; l <= L; ++l) {
+        const int sz = b >> l, nn = NB << l;
+        int k = std::min(kmax, sz);
+        k -= k & 1;
+        if (k < 2) k = 2;
+        if (node_svd_kz<T>(sz, k) == 0) return fail(ACR_ERR_INVALID_ARG, "HODLR node %d too large", sz);
+        kl[l] = k;
+        std::vector<const T*> pa(nn), pb(nn);
+        std::vector<T*> pc(nn);
+        DevBuf Y;
+        CK(Y.alloc((size_t)nn * sz * k * sizeof(T), s));
+        CK(Uk[l].alloc((size_t)nn * sz * k * sizeof(T), s));
+        CK(Vk[l].alloc((size_t)nn * sz * k * sizeof(T), s));
+        CK(Sg[l].alloc((size_t)nn * k * sizeof(T), s));
+        for (int g = 0; g < NB; ++g)
+            for (int ni = 0; ni < (1 << l); ++ni) {
+                const int p = ni >> 1, lower = ni & 1;
+                const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
+                const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
+                const size_t id = ((size_t)g << l) + ni;
+                pa[id] = blocks[g] + r0 + (size_t)c0 * b;
+                pb[id] = om.as<T>();
+                pc[id] = Y.as<T>() + id * sz * k;
+            }
+        DevBuf dpa, dpb, dpc;
+        CK(dpa.alloc(nn * sizeof(void*), s));
+        CK(dpb.alloc(nn * sizeof(void*), s));
+        CK(dpc.alloc(nn * sizeof(void*), s));
+        CK(cudaMemcpyAsync(dpa.p, pa.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dpb.p, pb.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dpc.p, pc.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(gemm_gen<T>(dpa.as<const T*>(), dpb.as<const T*>(), dpc.as<T*>(), nn, sz, k, sz, b, omr, sz, false, s));
+        CK(node_svd<T>(Y.as<T>(), Uk[l].as<T>(), Sg[l].as<T>(), nn, sz, k, s));
+        // V_k = B^T U_k
+        for (int i = 0; i < nn; ++i) {
+            pb[i] = Uk[l].as<T>() + (size_t)i * sz * k;
+            pc[i] = Vk[l].as<T>() + (size_t)i * sz * k;
+        }
+        CK(cudaStreamSynchronize(s));  // host pointer tables reused below
+        CK(cudaMemcpyAsync(dpb.p, pb.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dpc.p, pc.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(gemm_gen<T>(dpa.as<const T*>(), dpb.as<const T*>(), dpc.as<T*>(), nn, sz, k, sz, b, sz, sz, true, s));
+        hsig[l].resize((size_t)nn * k);
+        CK(cudaMemcpyAsync(hsig[l].data(), Sg[l].p, (size_t)nn * k * sizeof(T), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+
+    // ---- ranks, layout ------------------------------------------------------------
+    std::vector<HNode> nodes((size_t)NB * npb);
+    std::vector<HBlk> hb(NB);
+    long long off = (long long)NB * b * leaf;  // leaves first
+    for (int g = 0; g < NB; ++g) {
+        hb[g].leaf_off = (long long)g * b * leaf;
+        hb[g].node_base = g * npb;
+        hb[g].pad = 0;
+    }
+    std::vector<double> rsum(h->levels(), 0.0);
+    std::vector<long long> rcnt(h->levels(), 0);
+    std::vector<int> rmax(h->levels(), 0);
+    std::vector<int> blk_level(NB, 0);
+    for (int t = 0; t <= T_; ++t)
+        for (int arr = 0; arr < 5; ++arr)
+            for (int id : h->bid[t][arr])
+                if (id >= 0) blk_level[id] = t;
+    for (int l = 1; l <= L; ++l) {
+        const int sz = b >> l, k = kl[l];
+        for (int g = 0; g < NB; ++g)
+            for (int ni = 0; ni < (1 << l); ++ni) {
+                const size_t id = ((size_t)g << l) + ni;
+                const T* sg = hsig[l].data() + id * k;
+                int r = 0;
+                if (sg[0] > T(0))
+                    while (r < k && (double)sg[r] > tol * (double)sg[0]) ++r;
+                if (max_rank > 0 && r > max_rank) r = max_rank;
+                const bool sketch_full = (k < sz) && (r > k - 4);
+                const bool dense = sketch_full || (2 * r >= sz);
+                HNode& hn = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
+                hn.pad = 0;
+                hn.off = off;
+                if (dense) {
+                    hn.rank = -1;
+                    off += (long long)sz * sz;
+                } else {
+                    hn.rank = r;
+                    off += 2LL * sz * r;
+                }
+                const int t = blk_level[g];
+                const int rr = dense ? sz : r;
+                rsum[t] += rr;
+                rcnt[t] += 1;
+                rmax[t] = std::max(rmax[t], rr);
+            }
+    }
+    const size_t pool_bytes = (size_t)off * sizeof(T);
+    CK(h->hpool.alloc_sync(pool_bytes));
+    CK(h->hnodes.alloc_sync(std::max<size_t>(1, nodes.size()) * sizeof(HNode)));
+    CK(h->hblks.alloc_sync((size_t)NB * sizeof(HBlk)));
+    if (!nodes.empty())
+        CK(cudaMemcpyAsync(h->hnodes.p, nodes.data(), nodes.size() * sizeof(HNode), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->hblks.p, hb.data(), (size_t)NB * sizeof(HBlk), cudaMemcpyHostToDevice, s));
+
+    // ---- pack ----------------------------------------------------------------------
+    {
+        std::vector<long long> lo(NB);
+        for (int g = 0; g < NB; ++g) lo[g] = hb[g].leaf_off;
+        DevBuf dblk, dlo;
+        CK(dblk.alloc((size_t)NB * sizeof(void*), s));
+        CK(dlo.alloc((size_t)NB * sizeof(long long), s));
+        CK(cudaMemcpyAsync(dblk.p, blocks.data(), (size_t)NB * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dlo.p, lo.data(), (size_t)NB * sizeof(long long), cudaMemcpyHostToDevice, s));
+        CK(pack_leaves<T>(dblk.as<const T*>(), dlo.as<long long>(), NB, b, leaf, h->hpool.as<T>(), s));
+        for (int l = 1; l <= L; ++l) {
+            const int sz = b >> l, nn = NB << l;
+            std::vector<HNode> lv(nn);
+            std::vector<const T*> src(nn);
+            for (int g = 0; g < NB; ++g)
+                for (int ni = 0; ni < (1 << l); ++ni) {
+                    const size_t id = ((size_t)g << l) + ni;
+                    lv[id] = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
+                    const int p = ni >> 1, lower = ni & 1;
+                    const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
+                    const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
+                    src[id] = blocks[g] + r0 + (size_t)c0 * b;
+                }
+            DevBuf dm, ds;
+            CK(dm.alloc((size_t)nn * sizeof(HNode), s));
+            CK(ds.alloc((size_t)nn * sizeof(void*), s));
+            CK(cudaMemcpyAsync(dm.p, lv.data(), (size_t)nn * sizeof(HNode), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(ds.p, src.data(), (size_t)nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+            CK(pack_nodes<T>(dm.as<HNode>(), 0, nn, Uk[l].as<T>(), Vk[l].as<T>(), ds.as<const T*>(), sz, kl[l], b,
+                             h->hpool.as<T>(), s));
+            CK(cudaStreamSynchronize(s));  // host tables of this level
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+    // ---- keep the level-0 diagonals, release the dense arena ------------------------
+    if (h->band0 && T_ > 0) {
+        const Level& L0 = h->lev[0];
+        const size_t n4[4] = {(size_t)L0.ne * b, (size_t)L0.ne * b, (size_t)L0.nk * b, (size_t)L0.nk * b};
+        const size_t src4[4] = {L0.off_xa, L0.off_xc, L0.off_ak, L0.off_ck};
+        size_t tot = 0;
+        for (int i = 0; i < 4; ++i) { h->hd_off[i] = tot; tot += n4[i]; }
+        CK(h->hdiag.alloc_sync(std::max<size_t>(tot, 1) * sizeof(T)));
+        for (int i = 0; i < 4; ++i)
+            CK(cudaMemcpyAsync(h->hdiag.as<T>() + h->hd_off[i], h->P<T>(src4[i]), n4[i] * sizeof(T),
+                               cudaMemcpyDeviceToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    h->hblk_bytes.assign(NB, (double)b * leaf * sizeof(T));
+    for (int g = 0; g < NB; ++g)
+        for (int i = 0; i < npb; ++i) {
+            const HNode& hn = nodes[(size_t)g * npb + i];
+            int l = 1;
+            while (((1 << (l + 1)) - 2) <= i) ++l;
+            const int sz = b >> l;
+            h->hblk_bytes[g] += (hn.rank < 0 ? (double)sz * sz : 2.0 * sz * hn.rank) * sizeof(T);
+        }
+    h->arena.release();
+    h->compressed = true;
+    h->st.compressed = 1;
+    h->st.factor_bytes = pool_bytes + nodes.size() * sizeof(HNode) + (size_t)NB * sizeof(HBlk) +
+                         (h->band0 ? (size_t)(h->lev[0].ne + h->lev[0].nk) * 2 * b * sizeof(T) : 0);
+    for (int t = 0; t <= T_ && t < 32; ++t) {
+        h->st.rank_max[t] = rmax[t];
+        h->st.rank_mean[t] = rcnt[t] ? rsum[t] / (double)rcnt[t] : 0.0;
+    }
+    return ACR_OK;
 }
 
 template <class T>
@@ -539,6 +783,23 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     h->st.inv_launches = inv_l;
     h->st.gemm_launches = gemm_l;
     h->st.launches_factor = launch_count() - l0 + 1;  // + the staging kernel
+    if (h->tol > 0) {
+        const long long c0 = launch_count();
+        cudaEvent_t ce0, ce1;
+        CK(cudaEventCreate(&ce0));
+        CK(cudaEventCreate(&ce1));
+        CK(cudaEventRecord(ce0, s));
+        const int st = compress_factor<T>(h);
+        if (st != ACR_OK) return st;
+        CK(cudaEventRecord(ce1, s));
+        CK(cudaEventSynchronize(ce1));
+        float cms = 0.f;
+        cudaEventElapsedTime(&cms, ce0, ce1);
+        cudaEventDestroy(ce0);
+        cudaEventDestroy(ce1);
+        h->st.factor_ms += cms;
+        h->st.launches_factor += launch_count() - c0;
+    }
     return ACR_OK;
 }
 
@@ -549,6 +810,8 @@ template <class T>
 struct SweepPlan {
     DevBuf ws;       // level vectors F_t (t >= 1) and G_t
     DevBuf dprobs;
+    DevBuf hprobs;   // the same problems on compressed blocks
+    bool hodlr = false;
     std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
     int nrhs = 0;
     double bytes = 0.0;             // algorithmic bytes of one pass
@@ -586,6 +849,19 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
     auto Fp = [&](int t) { return t == 0 ? F0 : base + foff[t]; };
     auto Gp = [&](int t) { return base + goff[t]; };
     std::vector<SweepProb<T>> pr;
+    // compressed blocks: the same problems on HODLR blocks (ids) instead of
+    // dense block pointers
+    std::vector<HSweepProb<T>> hp;
+    const bool H = h->compressed;
+    auto toh = [](const SweepProb<T>& p) {
+        HSweepProb<T> q;
+        memset(&q, 0, sizeof(q));
+        q.out = p.out; q.cin = p.cin; q.ldo = p.ldo; q.ldc = p.ldc; q.ldx = p.ldx; q.alpha = p.alpha;
+        q.x[0] = p.x[0]; q.x[1] = p.x[1];
+        q.blk[0] = q.blk[1] = -1;
+        return q;
+    };
+    const T* hd = H && h->band0 ? h->hdiag.template as<T>() : nullptr;
     sp.fw_g_off.assign(T_ + 1, 0); sp.fw_g_cnt.assign(T_ + 1, 0);
     sp.fw_f_off.assign(T_ + 1, 0); sp.fw_f_cnt.assign(T_ + 1, 0);
     sp.bk_off.assign(T_ + 1, 0); sp.bk_cnt.assign(T_ + 1, 0);
@@ -605,6 +881,11 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
             p.m[0] = dinv + e * bb;
             p.x[0] = Fp(t) + (size_t)(2 * e) * b;
             pr.push_back(p);
+            if (H) {
+                HSweepProb<T> q = toh(p);
+                q.blk[0] = h->bid[t][0][e];
+                hp.push_back(q);
+            }
         }
         sp.fw_g_cnt[t] = pr.size() - sp.fw_g_off[t];
         sp.fw_f_off[t] = pr.size();
@@ -621,6 +902,17 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
                 p.x[0] = Gp(t) + (size_t)k * b;
                 if (i + 1 < L.m) { p.m[1] = ck + k * os; p.x[1] = Gp(t) + (size_t)(k + 1) * b; }
                 pr.push_back(p);
+                if (H) {
+                    HSweepProb<T> q = toh(p);
+                    if (h->band0 && t == 0) {
+                        q.dg[0] = hd + h->hd_off[2] + (size_t)k * b;
+                        if (i + 1 < L.m) q.dg[1] = hd + h->hd_off[3] + (size_t)k * b;
+                    } else {
+                        q.blk[0] = h->bid[t][3][k];
+                        if (i + 1 < L.m) q.blk[1] = h->bid[t][4][k];
+                    }
+                    hp.push_back(q);
+                }
             }
         }
         sp.fw_f_cnt[t] = pr.size() - sp.fw_f_off[t];
@@ -632,6 +924,7 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
         sp.bk_off[t] = pr.size();
         if (t == T_) {
             pr.push_back(mk(Fp(t), ldF, Gp(t), ldG, 0, T(0)));
+            if (H) hp.push_back(toh(pr.back()));
         } else {
             const T* xa = h->P<T>(L.off_xa);
             const T* xc = h->P<T>(L.off_xc);
@@ -640,6 +933,7 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
             for (int i = 0; i < L.m; ++i) {
                 if (i & 1) {
                     pr.push_back(mk(Fp(t) + (size_t)i * b, ldF, Un + (size_t)((i - 1) / 2) * b, ldU, 0, T(0)));
+                    if (H) hp.push_back(toh(pr.back()));
                 } else {
                     const int e = i / 2;
                     SweepProb<T> p = mk(Fp(t) + (size_t)i * b, ldF, Gp(t) + (size_t)e * b, ldG, ldU, T(-1));
@@ -654,6 +948,19 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
                         if (i + 1 < L.m) { p.m[1] = xc + e * bb; p.x[1] = Un + (size_t)(i / 2) * b; }
                     }
                     pr.push_back(p);
+                    if (H) {
+                        HSweepProb<T> q = toh(p);
+                        if (h->band0 && t == 0) {
+                            int nt = 0;
+                            if (i > 0) q.sx[nt++] = hd + h->hd_off[0] + (size_t)e * b;
+                            if (i + 1 < L.m) q.sx[nt++] = hd + h->hd_off[1] + (size_t)e * b;
+                            if (nt) q.blk[0] = h->bid[0][0][e];
+                        } else {
+                            if (i > 0) q.blk[0] = h->bid[t][1][e];
+                            if (i + 1 < L.m) q.blk[1] = h->bid[t][2][e];
+                        }
+                        hp.push_back(q);
+                    }
                 }
             }
         }
@@ -662,6 +969,24 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
     CK(sp.dprobs.alloc(pr.size() * sizeof(SweepProb<T>), s));
     CK(cudaMemcpyAsync(sp.dprobs.p, pr.data(), pr.size() * sizeof(SweepProb<T>), cudaMemcpyHostToDevice, s));
     sp.nrhs = nrhs;
+    sp.hodlr = H;
+    if (H) {
+        CK(sp.hprobs.alloc(hp.size() * sizeof(HSweepProb<T>), s));
+        CK(cudaMemcpyAsync(sp.hprobs.p, hp.data(), hp.size() * sizeof(HSweepProb<T>), cudaMemcpyHostToDevice, s));
+        const double pbh = (double)b * nrhs * sizeof(T);
+        sp.bytes = 0.0;
+        for (const HSweepProb<T>& q : hp) {
+            for (int t = 0; t < 2; ++t) {
+                if (q.dg[t]) sp.bytes += (double)b * sizeof(T) + pbh;
+                else if (q.blk[t] >= 0) sp.bytes += h->hblk_bytes[q.blk[t]] + pbh;
+            }
+            if (q.sx[0]) sp.bytes += (q.sx[1] ? 2.0 : 1.0) * b * sizeof(T) + (q.x[1] ? pbh : 0.0);
+            if (q.cin) sp.bytes += pbh;
+            sp.bytes += pbh;
+        }
+        CK(cudaStreamSynchronize(s));  // host tables go out of scope
+        return ACR_OK;
+    }
     // algorithmic traffic: every block read once, every panel operand read
     // once and every output panel written once
     const double pb = (double)b * nrhs * sizeof(T);
@@ -691,11 +1016,25 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
     sp.evs.push_back(e1);
     const long long c0 = launch_count();
     CK(cudaEventRecord(e0, s));
-    for (int t = 0; t <= T_; ++t) {
-        CK(sweep_batched<T>(dp + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], b, nrhs, s));
-        if (sp.fw_f_cnt[t]) CK(sweep_batched<T>(dp + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], b, nrhs, s));
+    if (sp.hodlr) {
+        const HSweepProb<T>* hq = sp.hprobs.template as<HSweepProb<T>>();
+        const HBlk* hb = h->hblks.as<HBlk>();
+        const HNode* hn = h->hnodes.as<HNode>();
+        const T* pool = h->hpool.as<T>();
+        for (int t = 0; t <= T_; ++t) {
+            CK(hsweep<T>(hq + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
+            if (sp.fw_f_cnt[t])
+                CK(hsweep<T>(hq + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
+        }
+        for (int t = T_; t >= 0; --t)
+            CK(hsweep<T>(hq + sp.bk_off[t], (int)sp.bk_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
+    } else {
+        for (int t = 0; t <= T_; ++t) {
+            CK(sweep_batched<T>(dp + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], b, nrhs, s));
+            if (sp.fw_f_cnt[t]) CK(sweep_batched<T>(dp + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], b, nrhs, s));
+        }
+        for (int t = T_; t >= 0; --t) CK(sweep_batched<T>(dp + sp.bk_off[t], (int)sp.bk_cnt[t], b, nrhs, s));
     }
-    for (int t = T_; t >= 0; --t) CK(sweep_batched<T>(dp + sp.bk_off[t], (int)sp.bk_cnt[t], b, nrhs, s));
     CK(cudaEventRecord(e1, s));
     sp.launches += launch_count() - c0;
     return ACR_OK;
@@ -1068,7 +1407,6 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     if (op.m_stop > 1) return fail(ACR_ERR_INVALID_ARG, "m_stop > 1 is not supported (reduction runs to one block)");
     if (op.ir_max_iter <= 0) op.ir_max_iter = 20;
     if (!(op.ir_tol > 0)) op.ir_tol = 1e-8;
-    if (tol > 0) return fail(ACR_ERR_INVALID_ARG, "compressed (HODLR) blocks: tol > 0 not available in this build");
     acr_ctx* h = new (std::nothrow) acr_ctx();
     if (!h) return fail(ACR_ERR_OOM, "host allocation failed");
     h->n = nblk; h->b = blksz; h->prec = op.precision; h->in_kind = op.input_kind; h->tol = tol; h->opts = op;
@@ -1083,6 +1421,8 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
         h->own_stream = true;
     }
     h->es = op.precision == ACR_FP64 ? 8 : 4;
+    // ranks below the factor's own rounding level only encode noise
+    h->tol_eff = tol > 0 ? std::max(tol, (h->es == 8 ? 32 * 2.220446049250313e-16 : 32 * 1.1920929e-7)) : 0.0;
     h->st.nblk = nblk; h->st.blksz = blksz; h->st.precision = op.precision; h->st.compressed = 0;
     int st = (h->es == 8) ? run_factor<double>(h, A, D, C) : run_factor<float>(h, A, D, C);
     if (st != ACR_OK) {

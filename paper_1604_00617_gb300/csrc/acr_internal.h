@@ -110,6 +110,54 @@ int tc_encode_map(void* map_out, const float* base, int b, int count, int role);
 // d_err: set to 1 if a CTA gave up on a bounded wait (then later CTAs skip).
 cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s);
 
+// --- HODLR blocks (k_hodlr.cu) ------------------------------------------------
+// Node of a compressed block: rank >= 0: U (s x rank) then V (s x rank) at off
+// (B ~= U V^T); rank -1: the dense s x s node at off.  Nodes of a block are
+// stored tree level by level (level l: 2^l nodes; node 2p+0 is the upper and
+// 2p+1 the lower off-diagonal block of parent p).
+struct HNode {
+    long long off;
+    int rank;
+    int pad;
+};
+struct HBlk {
+    long long leaf_off;  // 2^L leaves of leaf x leaf, column-major, contiguous
+    int node_base;       // first node of this block in the node table
+    int pad;
+};
+// Sweep problem on compressed blocks: out = cin + alpha * sum_t term_t with
+// term_t = M_{blk[t]} x[t] (combined mode as SweepProb: sx[0] set) or, when
+// dg[t] is set, the diagonal product dg[t] .* x[t].
+template <class T>
+struct HSweepProb {
+    T* out;
+    const T* cin;
+    long long ldo, ldc, ldx;
+    const T* x[2];
+    const T* sx[2];
+    const T* dg[2];
+    int blk[2];
+    T alpha;
+};
+template <class T>
+cudaError_t hodlr_omega(T* om, long long n, uint64_t seed, cudaStream_t s);
+template <class T>
+cudaError_t gemm_gen(const T* const* A, const T* const* B, T* const* C, int nprob, int M, int N, int K, int lda,
+                     int ldb, int ldc, bool transA, cudaStream_t s);
+template <class T>
+cudaError_t node_svd(const T* Y, T* U, T* sig, int nnodes, int s, int k, cudaStream_t st);
+template <class T>
+int node_svd_kz(int s, int k);
+template <class T>
+cudaError_t pack_nodes(const HNode* meta, int node0, int nnodes, const T* Uk, const T* Vk, const T* const* src,
+                       int s, int k, int b, T* pool, cudaStream_t st);
+template <class T>
+cudaError_t pack_leaves(const T* const* blocks, const long long* leaf_off, int nblocks, int b, int leaf, T* pool,
+                        cudaStream_t st);
+template <class T>
+cudaError_t hsweep(const HSweepProb<T>* probs, int nprob, const HBlk* blks, const HNode* nodes, const T* pool, int b,
+                   int leaf, int L, int nrhs, cudaStream_t s);
+
 // --- batched block x multi-vector (solve sweeps, dense FP64 residual) ----
 template <class T>
 cudaError_t sweep_batched(const SweepProb<T>* d_probs, int nprob, int b, int nrhs, cudaStream_t s);

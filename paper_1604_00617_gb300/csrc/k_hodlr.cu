@@ -1,0 +1,578 @@
+// k_hodlr.cu -- HODLR (hierarchically off-diagonal low-rank) blocks.
+//
+// Section 3 holds every block of the reduction as an H-matrix with weak
+// admissibility, i.e. a HODLR matrix: a balanced binary tree over the rows of
+// a b x b block; at tree level l (1..L) every node of size s = b / 2^l has
+// two off-diagonal blocks (upper: rows of its first child x columns of its
+// second child, lower: the converse) stored as U V^T with a rank set by the
+// tolerance; the 2^L diagonal leaves of size leaf = b / 2^L are dense.
+//
+// Recompression of one off-diagonal block B (s x s), batched over all blocks:
+//   Y = B Omega                       (s x k sketch, Omega Gaussian, seeded)
+//   Y = Q R                           (Householder QR, in shared memory)
+//   R = W S Z^T                       (one-sided Jacobi SVD of the k x k R)
+//   U_k = Q W,   V_k = B^T U_k         (so that U_k U_k^T B = U_k V_k^T)
+//   rank r = #{ sigma_i > tol * sigma_1 }, capped;  keep U_k[:, :r], V_k[:, :r]
+// A node whose rank reaches k - 4 (the sketch cannot certify it) is kept
+// dense.  Then B ~= U V^T with error ~ sigma_{r+1}(B).
+//
+// Apply (solve sweeps): y += M x = leaves * x + sum_nodes U (V^T x), tree
+// level by tree level (nodes of one level touch disjoint rows, so the sum
+// order is fixed).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+// ---------------------------------------------------------------- Omega
+// Counter-based Gaussian: a 64-bit mix of (seed, index) gives two uniforms,
+// Box-Muller turns them into one normal deviate.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_omega(T* __restrict__ om, long long n, uint64_t seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint64_t h = mix64(seed ^ mix64((uint64_t)i));
+        const double u1 = ((h >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+        const double u2 = (double)(mix64(h) >> 11) * (1.0 / 9007199254740992.0);
+        om[i] = (T)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+}
+
+template <class T>
+cudaError_t hodlr_omega(T* om, long long n, uint64_t seed, cudaStream_t s) {
+    k_omega<T><<<304, 256, 0, s>>>(om, n, seed);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- GEMM
+// Batched C_p = op(A_p) B_p, uniform M, N, K and leading dimensions; op(A) =
+// A (M x K, column-major) or A^T (A stored K x M).  SIMT, 64 x 32 tiles.
+template <class T, bool TA>
+__global__ void __launch_bounds__(256)
+k_gemm_gen(const T* const* __restrict__ Ap, const T* const* __restrict__ Bp, T* const* __restrict__ Cp, int M, int N,
+           int K, int lda, int ldb, int ldc) {
+    constexpr int BM = 64, BN = 32, BK = 16, TM = 4, TN = 2, RY = BM / TM;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const T* A = Ap[blockIdx.y];
+    const T* B = Bp[blockIdx.y];
+    T* C = Cp[blockIdx.y];
+    const int tiles_m = (M + BM - 1) / BM;
+    const int row0 = (blockIdx.x % tiles_m) * BM, col0 = (blockIdx.x / tiles_m) * BN;
+    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int i = tid; i < BM * BK; i += 256) {
+            int r, k;
+            if (TA) { k = i % BK; r = i / BK; } else { r = i % BM; k = i / BM; }
+            const int gr = row0 + r, gk = k0 + k;
+            T v = T(0);
+            if (gr < M && gk < K) v = TA ? A[gk + (size_t)gr * lda] : A[gr + (size_t)gk * lda];
+            As[k][r] = v;
+        }
+        for (int i = tid; i < BK * BN; i += 256) {
+            const int k = i % BK, c = i / BK;
+            const int gk = k0 + k, gc = col0 + c;
+            Bs[k][c] = (gk < K && gc < N) ? B[gk + (size_t)gc * ldb] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            T af[TM], bf[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) af[i] = As[k][ty + i * RY];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bf[j] = Bs[k][tx + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const int c = col0 + tx + j * (BN / TN);
+        if (c >= N) continue;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + ty + i * RY;
+            if (r < M) C[r + (size_t)c * ldc] = acc[i][j];
+        }
+    }
+}
+
+template <class T>
+cudaError_t gemm_gen(const T* const* A, const T* const* B, T* const* C, int nprob, int M, int N, int K, int lda,
+                     int ldb, int ldc, bool transA, cudaStream_t s) {
+    if (nprob <= 0) return cudaSuccess;
+    const int tiles = ((M + 63) / 64) * ((N + 31) / 32);
+    int done = 0;
+    while (done < nprob) {  // grid.y is limited to 65535
+        const int cnt = std::min(nprob - done, 65535);
+        dim3 g(tiles, cnt);
+        if (transA)
+            k_gemm_gen<T, true><<<g, 256, 0, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc);
+        else
+            k_gemm_gen<T, false><<<g, 256, 0, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- node SVD
+// One CTA per node: Y (s x k) -> Householder QR -> Jacobi SVD of R -> U_k = Q W
+// (columns by decreasing singular value) and the singular values.
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T* __restrict__ Uall,
+                                                   T* __restrict__ sig_all, int s, int k, int kz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Y = reinterpret_cast<T*>(smem_raw);   // s x k, column-major (ld s); becomes the reflectors
+    T* R = Y + (size_t)s * k;                // k x k (ld k)
+    T* tau = R + (size_t)k * k;              // k
+    T* sv = tau + k;                         // k
+    T* Z = sv + k;                           // s x kz work panel
+    int* ord = reinterpret_cast<int*>(Z + (size_t)s * kz);  // k
+    __shared__ T red[8];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t node = blockIdx.x;
+    const T* Yg = Yall + node * (size_t)s * k;
+    for (int i = tid; i < s * k; i += 256) Y[i] = Yg[i];
+    __syncthreads();
+    // ---- Householder QR (LAPACK convention: H = I - tau v v^T, v[0] = 1) ----
+    for (int j = 0; j < k; ++j) {
+        T* col = Y + (size_t)j * s;
+        // ||x[1:]||^2
+        T part = T(0);
+        for (int r = j + 1 + tid; r < s; r += 256) part += col[r] * col[r];
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            T xn2 = T(0);
+            for (int w = 0; w < 8; ++w) xn2 += red[w];
+            const T alpha = col[j];
+            if (xn2 == T(0)) {
+                tau[j] = T(0);
+                R[j + j * k] = alpha;
+                red[0] = T(0);  // scale for v
+                s_flag = 0;
+            } else {
+                T beta = sqrt(alpha * alpha + xn2);
+                if (alpha > T(0)) beta = -beta;
+                tau[j] = (beta - alpha) / beta;
+                R[j + j * k] = beta;
+                red[0] = T(1) / (alpha - beta);
+                s_flag = 1;
+            }
+        }
+        __syncthreads();
+        const T scl = red[0];
+        const bool active = s_flag != 0;
+        if (active)
+            for (int r = j + 1 + tid; r < s; r += 256) col[r] *= scl;
+        __syncthreads();
+        if (tid == 0) col[j] = T(1);
+        __syncthreads();
+        // apply H_j to columns j+1..k-1: one warp per column
+        const T tj = tau[j];
+        for (int c = j + 1 + warp; c < k; c += 8) {
+            T* cc = Y + (size_t)c * s;
+            T d = T(0);
+            for (int r = j + lane; r < s; r += 32) d += col[r] * cc[r];
+            d = warp_sum(d) * tj;
+            for (int r = j + lane; r < s; r += 32) cc[r] -= d * col[r];
+        }
+        __syncthreads();
+    }
+    // R: upper triangle (row j of column c > j is Y[j, c] after the sweep)
+    for (int i = tid; i < k * k; i += 256) {
+        const int r = i % k, c = i / k;
+        if (r < c) R[r + c * k] = Y[r + (size_t)c * s];
+        else if (r > c) R[r + c * k] = T(0);
+    }
+    __syncthreads();
+    // ---- one-sided Jacobi on the columns of R (round-robin pairs) -----------
+    const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        if (tid == 0) s_flag = 0;
+        __syncthreads();
+        for (int rnd = 0; rnd < k - 1; ++rnd) {
+            for (int q = warp; q < k / 2; q += 8) {
+                int a, bcol;
+                if (q == 0) { a = k - 1; bcol = rnd; }
+                else { a = (rnd + q) % (k - 1); bcol = (rnd - q + (k - 1)) % (k - 1); }
+                T* ca = R + a * k;
+                T* cb = R + bcol * k;
+                T al = T(0), be = T(0), ga = T(0);
+                for (int r = lane; r < k; r += 32) {
+                    const T x = ca[r], y = cb[r];
+                    al += x * x; be += y * y; ga += x * y;
+                }
+                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                if (fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                    const T zeta = (be - al) / (T(2) * ga);
+                    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+                    for (int r = lane; r < k; r += 32) {
+                        const T x = ca[r], y = cb[r];
+                        ca[r] = c * x - sn * y;
+                        cb[r] = sn * x + c * y;
+                    }
+                    if (lane == 0) s_flag = 1;
+                }
+            }
+            __syncthreads();
+        }
+        // every thread reads the flag before thread 0 may reset it for the
+        // next sweep, so all threads leave the loop on the same sweep
+        const bool converged = !s_flag;
+        __syncthreads();
+        if (converged) break;
+    }
+    // singular values and their order (decreasing, ties by index)
+    for (int c = warp; c < k; c += 8) {
+        T n2 = T(0);
+        for (int r = lane; r < k; r += 32) n2 += R[r + c * k] * R[r + c * k];
+        n2 = warp_sum(n2);
+        if (lane == 0) sv[c] = sqrt(n2);
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += 256) {  // total order (NaN lowest, ties by index): a permutation
+        const T vc = isnan(sv[c]) ? T(-1) : sv[c];
+        int pos = 0;
+        for (int j = 0; j < k; ++j) {
+            const T vj = isnan(sv[j]) ? T(-1) : sv[j];
+            pos += (vj > vc) || (vj == vc && j < c);
+        }
+        ord[pos] = c;
+    }
+    __syncthreads();
+    T* sg = sig_all + node * k;
+    for (int i = tid; i < k; i += 256) sg[i] = sv[ord[i]];
+    // ---- U_k = Q [W; 0], W = R J normalised, in panels of kz columns --------
+    T* Ug = Uall + node * (size_t)s * k;
+    for (int c0 = 0; c0 < k; c0 += kz) {
+        const int nc = std::min(kz, k - c0);
+        for (int i = tid; i < s * nc; i += 256) {
+            const int r = i % s, c = i / s;
+            const int src = ord[c0 + c];
+            const T nv = sv[src];
+            Z[r + (size_t)c * s] = (r < k && nv > T(0)) ? R[r + src * k] / nv : T(0);
+        }
+        __syncthreads();
+        for (int j = k - 1; j >= 0; --j) {
+            const T* v = Y + (size_t)j * s;
+            const T tj = tau[j];
+            if (tj == T(0)) continue;
+            for (int c = warp; c < nc; c += 8) {
+                T* zc = Z + (size_t)c * s;
+                T d = T(0);
+                for (int r = j + lane; r < s; r += 32) d += v[r] * zc[r];
+                d = warp_sum(d) * tj;
+                for (int r = j + lane; r < s; r += 32) zc[r] -= d * v[r];
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < s * nc; i += 256) {
+            const int r = i % s, c = i / s;
+            Ug[r + (size_t)(c0 + c) * s] = Z[r + (size_t)c * s];
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+size_t node_svd_smem(int s, int k, int kz) {
+    return ((size_t)s * k + (size_t)k * k + 2 * (size_t)k + (size_t)s * kz) * sizeof(T) + (size_t)k * sizeof(int);
+}
+
+template <class T>
+int node_svd_kz(int s, int k) {  // widest work panel that fits in 200 KB
+    for (int kz = k; kz >= 8; kz /= 2)
+        if (node_svd_smem<T>(s, k, kz) <= 200 * 1024) return kz;
+    return 0;
+}
+
+template <class T>
+cudaError_t node_svd(const T* Y, T* U, T* sig, int nnodes, int s, int k, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    const int kz = node_svd_kz<T>(s, k);
+    if (kz == 0) return cudaErrorInvalidValue;
+    const size_t sm = node_svd_smem<T>(s, k, kz);
+    cudaFuncSetAttribute(k_node_svd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int done = 0;
+    while (done < nnodes) {
+        const int cnt = std::min(nnodes - done, 1 << 30);
+        k_node_svd<T><<<cnt, 256, sm, st>>>(Y + (size_t)done * s * k, U + (size_t)done * s * k, sig + (size_t)done * k,
+                                             s, k, kz);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- packing
+// node i: rank r = meta[i].rank (-1: dense), destination offset meta[i].off;
+// U_k, V_k (s x k) or the dense block (src pointer, ld b).
+__global__ void k_dummy() {}
+
+template <class T>
+__global__ void k_pack_nodes(const HNode* __restrict__ meta, int node0, const T* __restrict__ Uk,
+                             const T* __restrict__ Vk, const T* const* __restrict__ src, int s, int k, int b,
+                             T* __restrict__ pool) {
+    const int i = blockIdx.x;
+    const HNode m = meta[node0 + i];
+    T* dst = pool + m.off;
+    if (m.rank < 0) {
+        const T* B = src[i];
+        for (int t = threadIdx.x; t < s * s; t += blockDim.x) {
+            const int r = t % s, c = t / s;
+            dst[t] = B[r + (size_t)c * b];
+        }
+    } else {
+        const int n = s * m.rank;
+        const T* u = Uk + (size_t)i * s * k;
+        const T* v = Vk + (size_t)i * s * k;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            dst[t] = u[t];
+            dst[n + t] = v[t];
+        }
+    }
+}
+
+template <class T>
+cudaError_t pack_nodes(const HNode* meta, int node0, int nnodes, const T* Uk, const T* Vk, const T* const* src,
+                       int s, int k, int b, T* pool, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    k_pack_nodes<T><<<nnodes, 256, 0, st>>>(meta, node0, Uk, Vk, src, s, k, b, pool);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// leaves: block g's 2^L diagonal leaf x leaf blocks, contiguous
+template <class T>
+__global__ void k_pack_leaves(const T* const* __restrict__ blocks, const long long* __restrict__ leaf_off, int b,
+                              int leaf, T* __restrict__ pool) {
+    const int g = blockIdx.y, li = blockIdx.x;
+    const T* B = blocks[g];
+    T* dst = pool + leaf_off[g] + (size_t)li * leaf * leaf;
+    const int o = li * leaf;
+    for (int t = threadIdx.x; t < leaf * leaf; t += blockDim.x) {
+        const int r = t % leaf, c = t / leaf;
+        dst[t] = B[(o + r) + (size_t)(o + c) * b];
+    }
+}
+
+template <class T>
+cudaError_t pack_leaves(const T* const* blocks, const long long* leaf_off, int nblocks, int b, int leaf, T* pool,
+                        cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    dim3 g(b / leaf, nblocks);
+    k_pack_leaves<T><<<g, 256, 0, st>>>(blocks, leaf_off, b, leaf, pool);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- apply
+// One CTA per problem.  x operands staged in shared memory (b x NR), y
+// accumulated in shared memory; leaves first, then tree levels 1..L (nodes of
+// one level write disjoint rows).
+template <class T, int NR>
+__global__ void __launch_bounds__(256)
+k_hsweep(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, const HNode* __restrict__ nodes,
+         const T* __restrict__ pool, int b, int leaf, int L, int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);  // b x NR
+    T* ys = xs + (size_t)b * NR;              // b x NR
+    T* ts = ys + (size_t)b * NR;              // 8 warps x 64 x NR (node products)
+    const HSweepProb<T> P = probs[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = std::min(NR, nrhs - q0);
+        for (int i = tid; i < b * NR; i += 256) ys[i] = T(0);
+        __syncthreads();
+        for (int t = 0; t < 2; ++t) {
+            if (!P.x[t]) continue;
+            const bool diag = P.dg[t] != nullptr;
+            if (diag) {
+                for (int i = tid; i < b * NR; i += 256) {
+                    const int r = i % b, q = i / b;
+                    if (q < nq) ys[r * NR + q] += P.dg[t][r] * P.x[t][r + (size_t)(q0 + q) * P.ldx];
+                }
+                __syncthreads();
+                continue;
+            }
+            if (P.blk[t] < 0) continue;
+            // stage x (combined mode: sx[0] .* x[0] + sx[1] .* x[1] for term 0)
+            const bool comb = (t == 0) && P.sx[0] != nullptr;
+            for (int i = tid; i < b * NR; i += 256) {
+                const int r = i % b, q = i / b;
+                T v = T(0);
+                if (q < nq) {
+                    const size_t o = r + (size_t)(q0 + q) * P.ldx;
+                    if (comb) {
+                        v = P.sx[0][r] * P.x[0][o];
+                        if (P.x[1]) v += P.sx[1][r] * P.x[1][o];
+                    } else {
+                        v = P.x[t][o];
+                    }
+                }
+                xs[r * NR + q] = v;
+            }
+            __syncthreads();
+            const HBlk B = blks[P.blk[t]];
+            // leaves: thread per (row), NR accumulators
+            for (int r = tid; r < b; r += 256) {
+                const int li = r / leaf, rr = r % leaf;
+                const T* Lm = pool + B.leaf_off + (size_t)li * leaf * leaf;
+                T acc[NR];
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                for (int c = 0; c < leaf; ++c) {
+                    const T m = Lm[rr + (size_t)c * leaf];
+                    const T* xc = xs + (li * leaf + c) * NR;
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) acc[q] = fma(m, xc[q], acc[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < NR; ++q) ys[r * NR + q] += acc[q];
+            }
+            __syncthreads();
+            // off-diagonal nodes, one tree level at a time
+            int nb = B.node_base;
+            for (int l = 1; l <= L; ++l) {
+                const int s = b >> l, nn = 1 << l;
+                for (int ni = warp; ni < nn; ni += 8) {
+                    const HNode hn = nodes[nb + ni];
+                    const int p = ni >> 1, lower = ni & 1;
+                    const int r0 = lower ? (2 * p + 1) * s : 2 * p * s;   // output rows
+                    const int c0 = lower ? 2 * p * s : (2 * p + 1) * s;   // input rows of x
+                    const T* d = pool + hn.off;
+                    if (hn.rank < 0) {
+                        // dense node: y[r0 + i] += sum_j D[i, j] x[c0 + j]
+                        for (int i = lane; i < s; i += 32) {
+                            T acc[NR];
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                            for (int j = 0; j < s; ++j) {
+                                const T m = d[i + (size_t)j * s];
+#pragma unroll
+                                for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[(c0 + j) * NR + q], acc[q]);
+                            }
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) ys[(r0 + i) * NR + q] += acc[q];
+                        }
+                        continue;
+                    }
+                    const int rk = hn.rank;
+                    const T* U = d;
+                    const T* V = d + (size_t)s * rk;
+                    T* tw = ts + (size_t)warp * 64 * NR;
+                    // tw = V^T x[c0 : c0 + s]   (rk <= 64)
+                    for (int i = 0; i < rk; ++i) {
+                        T acc[NR];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                        for (int j = lane; j < s; j += 32) {
+                            const T m = V[j + (size_t)i * s];
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[(c0 + j) * NR + q], acc[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) {
+                            const T v = warp_sum(acc[q]);
+                            if (lane == 0) tw[i * NR + q] = v;
+                        }
+                    }
+                    __syncwarp();
+                    // y[r0 : r0 + s] += U tw
+                    for (int i = lane; i < s; i += 32) {
+                        T acc[NR];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                        for (int j = 0; j < rk; ++j) {
+                            const T m = U[i + (size_t)j * s];
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) acc[q] = fma(m, tw[j * NR + q], acc[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) ys[(r0 + i) * NR + q] += acc[q];
+                    }
+                    __syncwarp();
+                }
+                nb += nn;
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < b * NR; i += 256) {
+            const int r = i % b, q = i / b;
+            if (q < nq) {
+                T o = P.alpha * ys[r * NR + q];
+                if (P.cin) o += P.cin[r + (size_t)(q0 + q) * P.ldc];
+                P.out[r + (size_t)(q0 + q) * P.ldo] = o;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+cudaError_t hsweep(const HSweepProb<T>* probs, int nprob, const HBlk* blks, const HNode* nodes, const T* pool, int b,
+                   int leaf, int L, int nrhs, cudaStream_t s) {
+    if (nprob <= 0 || nrhs <= 0) return cudaSuccess;
+    const int NR = nrhs == 1 ? 1 : (nrhs <= 4 ? 4 : 8);
+    const size_t sm = ((size_t)2 * b * NR + (size_t)8 * 64 * NR) * sizeof(T);
+    if (sm > 200 * 1024) return cudaErrorInvalidValue;
+    if (NR == 1) {
+        cudaFuncSetAttribute(k_hsweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_hsweep<T, 1><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
+    } else if (NR == 4) {
+        cudaFuncSetAttribute(k_hsweep<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_hsweep<T, 4><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
+    } else {
+        cudaFuncSetAttribute(k_hsweep<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_hsweep<T, 8><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+#define ACR_HODLR_INST(T)                                                                                         \
+    template cudaError_t hodlr_omega<T>(T*, long long, uint64_t, cudaStream_t);                                   \
+    template cudaError_t gemm_gen<T>(const T* const*, const T* const*, T* const*, int, int, int, int, int, int,    \
+                                     int, bool, cudaStream_t);                                                    \
+    template cudaError_t node_svd<T>(const T*, T*, T*, int, int, int, cudaStream_t);                              \
+    template int node_svd_kz<T>(int, int);                                                                        \
+    template cudaError_t pack_nodes<T>(const HNode*, int, int, const T*, const T*, const T* const*, int, int, int, \
+                                       T*, cudaStream_t);                                                         \
+    template cudaError_t pack_leaves<T>(const T* const*, const long long*, int, int, int, T*, cudaStream_t);       \
+    template cudaError_t hsweep<T>(const HSweepProb<T>*, int, const HBlk*, const HNode*, const T*, int, int, int,  \
+                                   int, cudaStream_t);
+ACR_HODLR_INST(float)
+ACR_HODLR_INST(double)
+
+}  // namespace acr
