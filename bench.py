@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-blocks", type=int, default=32, help="oracle sample: leading grid lines")
+    p.add_argument("--tol", type=float, default=1e-8, help="HODLR compression tolerance (0: dense blocks)")
+    p.add_argument("--leaf", type=int, default=64, help="HODLR leaf size")
+    p.add_argument("--no-dense", action="store_true", help="skip the dense-block (tol 0) comparison")
     return p.parse_args()
 
 
@@ -248,6 +251,7 @@ def run_ours(args):
         o.input_kind = acr.ACR_BANDED
         o.ir_tol = 1e-8
         o.ir_max_iter = 60
+        o.leaf = args.leaf
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         return o
 
@@ -255,7 +259,7 @@ def run_ours(args):
     stats = []
 
     def step():
-        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, 0.0, o)
+        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, args.tol, o)
         try:
             dB.copy_(dF)
             res, it = acr.acr_solve_ex(h, dB, nrhs)
@@ -326,6 +330,7 @@ def run_ours(args):
                                    f"N={N}, {P.nblk} blocks of {P.b}x{P.b}, {nrhs} RHS, 16 points per wavelength "
                                    "+-20% seeded kappa, refinement to 1e-8",
                        "nblk": P.nblk, "blksz": P.b, "nrhs": nrhs, "precision": prec,
+                       "hodlr_tol": args.tol, "hodlr_leaf": args.leaf,
                        "l2": "inputs larger than L2 (factor storage %.1f GB vs 129 MB L2)" % (last["factor_bytes"] / 1e9),
                        "parallelism": f"replicas x{ws}"},
             "factor_s": statistics.median(s["factor_ms"] for s in stats) / 1e3,
@@ -336,13 +341,16 @@ def run_ours(args):
                         "inv_ms": last["inv_ms"], "inv_tflops": last["inv_flops"] / max(last["inv_ms"], 1e-9) / 1e9,
                         "sweep_ms": last["sweep_ms"],
                         "sweep_gbs": last["sweep_bytes"] / max(last["sweep_ms"], 1e-9) / 1e6},
+            "hodlr": {"tol": args.tol, "leaf": args.leaf, "compressed": bool(last["compressed"]),
+                      "factor_bytes": last["factor_bytes"],
+                      "rank_max": last["rank_max"], "rank_mean": [round(x, 2) for x in last["rank_mean"]]},
             "roofline": roof, "clocks": clocks,
             "gpu_launches": int(sum(s["launches_factor"] + s["launches_solve"] for s in stats))}
 
     # ---- FP64 comparator (same code, ACR_FP64), measured once ---------------
     if not args.no_fp64 and prec != "fp64":
         o64 = opts("fp64")
-        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, 0.0, o64)
+        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, args.tol, o64)
         try:
             dB.copy_(dF)
             try:
@@ -359,6 +367,19 @@ def run_ours(args):
                         "gemm_tflops": s["gemm_flops"] / s["gemm_ms"] / 1e9}
         line["time_to_1e8_s"] = (line["factor_s"] + line["solve_s"])
 
+    # ---- the same step with dense (uncompressed) blocks, measured once ------
+    if not args.no_dense and args.tol > 0:
+        h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, 0.0, o)
+        try:
+            dB.copy_(dF)
+            res, it = acr.acr_solve_ex(h, dB, nrhs)
+            s = acr.acr_stats(h)
+        finally:
+            acr.acr_free(h)
+        line["dense_blocks"] = {"factor_s": s["factor_ms"] / 1e3, "solve_s": s["solve_ms"] / 1e3, "iters": it,
+                                "factor_bytes": s["factor_bytes"], "resid_max": float(np.max(res)),
+                                "solves_per_s": nrhs / ((s["factor_ms"] + s["solve_ms"]) / 1e3)}
+
     # ---- end to end through the public API with host (pinned) buffers -----
     if not args.no_e2e:
         ha, hD3, hc = (torch.from_numpy(x).pin_memory() for x in (a, D3, c))
@@ -369,7 +390,7 @@ def run_ours(args):
         for k in range(1 + args.steps):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            h = acr.acr_factor_ex(P.nblk, P.b, ha, hD3, hc, 0.0, oe)
+            h = acr.acr_factor_ex(P.nblk, P.b, ha, hD3, hc, args.tol, oe)
             hB.copy_(hF)
             acr.acr_solve_ex(h, hB, nrhs)
             acr.acr_free(h)

@@ -143,6 +143,9 @@ struct acr_ctx {
     std::vector<std::vector<std::vector<int>>> bid;  // [level][array][slot] -> block id, -1 if unused
     size_t hd_off[4] = {0, 0, 0, 0};                 // element offsets of the 4 diagonal arrays in hdiag
     std::vector<double> hblk_bytes;                  // compressed bytes of every block
+    std::vector<HNode> hnodes_host;                  // host copies of the node / block tables
+    std::vector<HBlk> hblks_host;
+    int npb = 0;                                     // off-diagonal nodes per block
     std::mutex mu;
     acr_stats_t st{};
     ~acr_ctx() {
@@ -445,6 +448,9 @@ int compress_factor(acr_ctx* h) {
             const int sz = b >> l;
             h->hblk_bytes[g] += (hn.rank < 0 ? (double)sz * sz : 2.0 * sz * hn.rank) * sizeof(T);
         }
+    h->hnodes_host = nodes;
+    h->hblks_host = hb;
+    h->npb = npb;
     h->arena.release();
     h->compressed = true;
     h->st.compressed = 1;
@@ -811,6 +817,11 @@ struct SweepPlan {
     DevBuf ws;       // level vectors F_t (t >= 1) and G_t
     DevBuf dprobs;
     DevBuf hprobs;   // the same problems on compressed blocks
+    DevBuf htasks;   // their node tasks
+    DevBuf htbuf;    // node products V^T x
+    std::vector<size_t> task_start;  // first task of every problem (+ total)
+    DevBuf halist;                   // indices of the low-rank tasks
+    std::vector<size_t> a_start;     // first low-rank task (in halist) of every problem
     bool hodlr = false;
     std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
     int nrhs = 0;
@@ -971,6 +982,53 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
     sp.nrhs = nrhs;
     sp.hodlr = H;
     if (H) {
+        // node tasks of every compressed term (pass A of the apply), in problem order
+        std::vector<HTask> tasks;
+        long long tcount = 0;
+        sp.task_start.assign(hp.size() + 1, 0);
+        for (size_t pi = 0; pi < hp.size(); ++pi) {
+            sp.task_start[pi] = tasks.size();
+            HSweepProb<T>& q = hp[pi];
+            for (int t = 0; t < 2; ++t) {
+                q.tbase[t] = -1;
+                if (q.dg[t] || q.blk[t] < 0 || !q.x[t]) continue;
+                q.tbase[t] = (int)tasks.size();
+                const HBlk& hbk = h->hblks_host[q.blk[t]];
+                for (int nu = 0; nu < h->npb; ++nu) {
+                    int l = 1;
+                    while (((1 << (l + 1)) - 2) <= nu) ++l;
+                    const HNode& hn = h->hnodes_host[(size_t)hbk.node_base + nu];
+                    HTask tk;
+                    tk.node = hbk.node_base + nu;
+                    tk.prob = (int)pi;
+                    tk.term = t;
+                    tk.level = l;
+                    tk.ni = nu - ((1 << l) - 2);
+                    tk.pad = 0;
+                    tk.toff = hn.rank > 0 ? tcount : -1;
+                    if (hn.rank > 0) tcount += (long long)hn.rank * nrhs;
+                    tasks.push_back(tk);
+                }
+            }
+        }
+        sp.task_start[hp.size()] = tasks.size();
+        // pass A runs only the low-rank tasks: their indices, and per problem
+        // the first position in that list
+        std::vector<int> alist;
+        sp.a_start.assign(hp.size() + 1, 0);
+        for (size_t pi = 0; pi < hp.size(); ++pi) {
+            sp.a_start[pi] = alist.size();
+            for (size_t ti = sp.task_start[pi]; ti < sp.task_start[pi + 1]; ++ti)
+                if (tasks[ti].toff >= 0) alist.push_back((int)ti);
+        }
+        sp.a_start[hp.size()] = alist.size();
+        CK(sp.halist.alloc(std::max<size_t>(1, alist.size()) * sizeof(int), s));
+        if (!alist.empty())
+            CK(cudaMemcpyAsync(sp.halist.p, alist.data(), alist.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(sp.htasks.alloc(std::max<size_t>(1, tasks.size()) * sizeof(HTask), s));
+        if (!tasks.empty())
+            CK(cudaMemcpyAsync(sp.htasks.p, tasks.data(), tasks.size() * sizeof(HTask), cudaMemcpyHostToDevice, s));
+        CK(sp.htbuf.alloc(std::max<long long>(1, tcount) * sizeof(T), s));
         CK(sp.hprobs.alloc(hp.size() * sizeof(HSweepProb<T>), s));
         CK(cudaMemcpyAsync(sp.hprobs.p, hp.data(), hp.size() * sizeof(HSweepProb<T>), cudaMemcpyHostToDevice, s));
         const double pbh = (double)b * nrhs * sizeof(T);
@@ -1021,13 +1079,19 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
         const HBlk* hb = h->hblks.as<HBlk>();
         const HNode* hn = h->hnodes.as<HNode>();
         const T* pool = h->hpool.as<T>();
+        const HTask* tk = sp.htasks.template as<HTask>();
+        T* tb = sp.htbuf.template as<T>();
+        const int* al = sp.halist.template as<int>();
+        auto seg = [&](size_t off, size_t cnt) -> cudaError_t {
+            const size_t a0 = sp.a_start[off], a1 = sp.a_start[off + cnt];
+            return hsweep<T>(hq, (int)off, (int)cnt, tk, al, (int)a0, (int)(a1 - a0), tb, hb, hn, pool, b, h->leaf,
+                             h->hL, nrhs, s);
+        };
         for (int t = 0; t <= T_; ++t) {
-            CK(hsweep<T>(hq + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
-            if (sp.fw_f_cnt[t])
-                CK(hsweep<T>(hq + sp.fw_f_off[t], (int)sp.fw_f_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
+            CK(seg(sp.fw_g_off[t], sp.fw_g_cnt[t]));
+            if (sp.fw_f_cnt[t]) CK(seg(sp.fw_f_off[t], sp.fw_f_cnt[t]));
         }
-        for (int t = T_; t >= 0; --t)
-            CK(hsweep<T>(hq + sp.bk_off[t], (int)sp.bk_cnt[t], hb, hn, pool, b, h->leaf, h->hL, nrhs, s));
+        for (int t = T_; t >= 0; --t) CK(seg(sp.bk_off[t], sp.bk_cnt[t]));
     } else {
         for (int t = 0; t <= T_; ++t) {
             CK(sweep_batched<T>(dp + sp.fw_g_off[t], (int)sp.fw_g_cnt[t], b, nrhs, s));

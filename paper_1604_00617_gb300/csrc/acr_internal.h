@@ -137,7 +137,15 @@ struct HSweepProb {
     const T* sx[2];
     const T* dg[2];
     int blk[2];
+    int tbase[2];  // first task (of its npb node tasks) of each compressed term
     T alpha;
+};
+// One node product of the apply: t = V^T x (pass A).  toff: offset of t
+// (rank x nrhs, column-major) in the product buffer; -1 when the node is dense
+// or of rank 0.
+struct HTask {
+    int node, prob, term, level, ni, pad;
+    long long toff;
 };
 template <class T>
 cudaError_t hodlr_omega(T* om, long long n, uint64_t seed, cudaStream_t s);
@@ -154,9 +162,13 @@ cudaError_t pack_nodes(const HNode* meta, int node0, int nnodes, const T* Uk, co
 template <class T>
 cudaError_t pack_leaves(const T* const* blocks, const long long* leaf_off, int nblocks, int b, int leaf, T* pool,
                         cudaStream_t st);
+// Apply the problems probs_all[prob_off .. prob_off + nprob); their low-rank
+// node tasks are tasks[alist[a_off .. a_off + na)]; tbuf holds the node
+// products (pass A writes, pass B reads).
 template <class T>
-cudaError_t hsweep(const HSweepProb<T>* probs, int nprob, const HBlk* blks, const HNode* nodes, const T* pool, int b,
-                   int leaf, int L, int nrhs, cudaStream_t s);
+cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, const HTask* tasks, const int* alist,
+                   int a_off, int na, T* tbuf, const HBlk* blks, const HNode* nodes, const T* pool, int b, int leaf,
+                   int L, int nrhs, cudaStream_t s);
 
 // --- batched block x multi-vector (solve sweeps, dense FP64 residual) ----
 template <class T>

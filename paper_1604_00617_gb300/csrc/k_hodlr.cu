@@ -216,8 +216,25 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
     }
     __syncthreads();
     // ---- one-sided Jacobi on the columns of R (round-robin pairs) -----------
-    const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
-    for (int sweep = 0; sweep < 16; ++sweep) {
+    // Pairs of columns that are both negligible next to ||R||_F (below the
+    // precision of the data) are left alone: they cannot change the ranks.
+    const T eps = sizeof(T) == 8 ? T(4e-15) : T(4e-7);
+    {
+        T part = T(0);
+        for (int i = tid; i < k * k; i += 256) part += R[i] * R[i];
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            T f = T(0);
+            for (int w = 0; w < 8; ++w) f += red[w];
+            red[0] = f;
+        }
+        __syncthreads();
+    }
+    const T negl = red[0] * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
+    __syncthreads();
+    for (int sweep = 0; sweep < 12; ++sweep) {
         if (tid == 0) s_flag = 0;
         __syncthreads();
         for (int rnd = 0; rnd < k - 1; ++rnd) {
@@ -233,7 +250,7 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
                     al += x * x; be += y * y; ga += x * y;
                 }
                 al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                if (al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
                     const T zeta = (be - al) / (T(2) * ga);
                     const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                     const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
@@ -354,12 +371,15 @@ __global__ void k_pack_nodes(const HNode* __restrict__ meta, int node0, const T*
             dst[t] = B[r + (size_t)c * b];
         }
     } else {
-        const int n = s * m.rank;
+        // U column-major (s x rank); V stored transposed (rank x s, i.e. the
+        // rank values of one row contiguous) for the V^T x products
+        const int rk = m.rank, n = s * rk;
         const T* u = Uk + (size_t)i * s * k;
         const T* v = Vk + (size_t)i * s * k;
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             dst[t] = u[t];
-            dst[n + t] = v[t];
+            const int ii = t % rk, j = t / rk;
+            dst[n + t] = v[j + (size_t)ii * s];
         }
     }
 }
@@ -398,166 +418,215 @@ cudaError_t pack_leaves(const T* const* blocks, const long long* leaf_off, int n
 }
 
 // ---------------------------------------------------------------- apply
-// One CTA per problem.  x operands staged in shared memory (b x NR), y
-// accumulated in shared memory; leaves first, then tree levels 1..L (nodes of
-// one level write disjoint rows).
+// y = cin + alpha * sum_t M_t x_t for compressed M_t, in two passes:
+//   (A) one CTA per (problem, term, low-rank node): t_node = V^T x[cols],
+//       V stored transposed so a warp reads the rank values of a row at once;
+//   (B) one CTA per (problem, row tile): leaves, then per tree level the node
+//       whose rows contain the tile (U t_node, or the dense node times x).
+// Every output element is summed in a fixed order (leaf, level 1..L).
+template <class T>
+__device__ __forceinline__ T xval(const HSweepProb<T>& P, int term, int r, int q) {
+    const size_t o = r + (size_t)q * P.ldx;
+    if (term == 0 && P.sx[0]) {
+        T v = P.sx[0][r] * P.x[0][o];
+        if (P.x[1]) v += P.sx[1][r] * P.x[1][o];
+        return v;
+    }
+    return P.x[term][o];
+}
+
+// Pass A: t = V^T x for one low-rank node per CTA.  x[cols] is staged in
+// shared memory (coalesced); lane = g * rp + i handles rank index i (rp: rank
+// rounded up to a power of two, <= 32) for rows j = g, g + G, ... of its
+// warp's slice (G = 32 / rp), so small ranks still keep every lane busy.
+// Partial sums are combined across g by shuffles, across warps in shared
+// memory, in a fixed order.
 template <class T, int NR>
 __global__ void __launch_bounds__(256)
-k_hsweep(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, const HNode* __restrict__ nodes,
-         const T* __restrict__ pool, int b, int leaf, int L, int nrhs) {
+k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tasks, const int* __restrict__ alist,
+          const HNode* __restrict__ nodes, const T* __restrict__ pool, int b, int nrhs, T* __restrict__ tbuf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xs = reinterpret_cast<T*>(smem_raw);  // b x NR
-    T* ys = xs + (size_t)b * NR;              // b x NR
-    T* ts = ys + (size_t)b * NR;              // 8 warps x 64 x NR (node products)
-    const HSweepProb<T> P = probs[blockIdx.x];
+    T* xs = reinterpret_cast<T*>(smem_raw);          // s x NR
+    T* red = xs + (size_t)(b / 2) * NR;               // 8 warps x 64 ranks x NR
+    const HTask tk = tasks[alist[blockIdx.x]];
+    const HNode hn = nodes[tk.node];
+    const int rk = hn.rank;
+    const HSweepProb<T>& P = probs[tk.prob];
+    const int s = b >> tk.level, c0 = (tk.ni ^ 1) * s;
+    const T* Vt = pool + hn.off + (size_t)s * rk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rlo = rk < 32 ? rk : 32;
+    int rp = 1;
+    while (rp < rlo) rp <<= 1;
+    const int G = 32 / rp, g = lane / rp, i0 = lane % rp;
+    const int slice = (s + 7) / 8, j0 = warp * slice, j1 = min(s, j0 + slice);
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
-        const int nq = std::min(NR, nrhs - q0);
-        for (int i = tid; i < b * NR; i += 256) ys[i] = T(0);
+        const int nq = min(NR, nrhs - q0);
         __syncthreads();
+        for (int i = tid; i < s * NR; i += 256) {
+            const int c = i % s, q = i / s;
+            xs[c * NR + q] = q < nq ? xval(P, tk.term, c0 + c, q0 + q) : T(0);
+        }
+        __syncthreads();
+        for (int ib = 0; ib < rk; ib += 32) {  // rank indices ib + i0 (two passes when rk > 32)
+            const int ii = ib + i0;
+            const bool live = i0 < rp && ii < rk;
+            T acc[NR];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q] = T(0);
+            if (live) {
+#pragma unroll 4
+                for (int j = j0 + g; j < j1; j += G) {
+                    const T v = Vt[ii + (size_t)j * rk];
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) acc[q] = fma(v, xs[j * NR + q], acc[q]);
+                }
+            }
+            for (int o = rp; o < 32; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (g == 0 && live)
+#pragma unroll
+                for (int q = 0; q < NR; ++q) red[((size_t)warp * 64 + ii) * NR + q] = acc[q];
+        }
+        __syncthreads();
+        for (int i = tid; i < rk * NR; i += 256) {
+            const int ii = i % rk, q = i / rk;
+            if (q < nq) {
+                T sum = T(0);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) sum += red[((size_t)w * 64 + ii) * NR + q];
+                tbuf[tk.toff + ii + (size_t)(q0 + q) * rk] = sum;
+            }
+        }
+    }
+}
+
+template <class T, int NR>
+__global__ void __launch_bounds__(256)
+k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, const HNode* __restrict__ nodes,
+        const HTask* __restrict__ tasks, const T* __restrict__ tbuf, const T* __restrict__ pool, int b, int leaf,
+        int L, int nrhs, int RT) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int KG = 256 / RT;
+    T* xs = reinterpret_cast<T*>(smem_raw);           // up to (b/2) x NR
+    T* red = xs + (size_t)std::max(b / 2, leaf) * NR;  // KG x RT x NR
+    const HSweepProb<T>& P = probs[blockIdx.y];
+    const int R0 = blockIdx.x * RT;
+    const int tid = threadIdx.x, lr = tid % RT, g = tid / RT;
+    const int row = R0 + lr;
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = min(NR, nrhs - q0);
+        T acc[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = T(0);
         for (int t = 0; t < 2; ++t) {
             if (!P.x[t]) continue;
-            const bool diag = P.dg[t] != nullptr;
-            if (diag) {
-                for (int i = tid; i < b * NR; i += 256) {
-                    const int r = i % b, q = i / b;
-                    if (q < nq) ys[r * NR + q] += P.dg[t][r] * P.x[t][r + (size_t)(q0 + q) * P.ldx];
-                }
-                __syncthreads();
+            if (P.dg[t]) {
+                if (g == 0)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q)
+                        if (q < nq) acc[q] += P.dg[t][row] * P.x[t][row + (size_t)(q0 + q) * P.ldx];
                 continue;
             }
             if (P.blk[t] < 0) continue;
-            // stage x (combined mode: sx[0] .* x[0] + sx[1] .* x[1] for term 0)
-            const bool comb = (t == 0) && P.sx[0] != nullptr;
-            for (int i = tid; i < b * NR; i += 256) {
-                const int r = i % b, q = i / b;
-                T v = T(0);
-                if (q < nq) {
-                    const size_t o = r + (size_t)(q0 + q) * P.ldx;
-                    if (comb) {
-                        v = P.sx[0][r] * P.x[0][o];
-                        if (P.x[1]) v += P.sx[1][r] * P.x[1][o];
-                    } else {
-                        v = P.x[t][o];
-                    }
-                }
-                xs[r * NR + q] = v;
-            }
-            __syncthreads();
             const HBlk B = blks[P.blk[t]];
-            // leaves: thread per (row), NR accumulators
-            for (int r = tid; r < b; r += 256) {
-                const int li = r / leaf, rr = r % leaf;
-                const T* Lm = pool + B.leaf_off + (size_t)li * leaf * leaf;
-                T acc[NR];
-#pragma unroll
-                for (int q = 0; q < NR; ++q) acc[q] = T(0);
-                for (int c = 0; c < leaf; ++c) {
-                    const T m = Lm[rr + (size_t)c * leaf];
-                    const T* xc = xs + (li * leaf + c) * NR;
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) acc[q] = fma(m, xc[q], acc[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < NR; ++q) ys[r * NR + q] += acc[q];
+            // leaf
+            const int li = R0 / leaf, rr = row - li * leaf;
+            __syncthreads();
+            for (int i = tid; i < leaf * NR; i += 256) {
+                const int c = i % leaf, q = i / leaf;
+                xs[c * NR + q] = q < nq ? xval(P, t, li * leaf + c, q0 + q) : T(0);
             }
             __syncthreads();
-            // off-diagonal nodes, one tree level at a time
-            int nb = B.node_base;
-            for (int l = 1; l <= L; ++l) {
-                const int s = b >> l, nn = 1 << l;
-                for (int ni = warp; ni < nn; ni += 8) {
-                    const HNode hn = nodes[nb + ni];
-                    const int p = ni >> 1, lower = ni & 1;
-                    const int r0 = lower ? (2 * p + 1) * s : 2 * p * s;   // output rows
-                    const int c0 = lower ? 2 * p * s : (2 * p + 1) * s;   // input rows of x
-                    const T* d = pool + hn.off;
-                    if (hn.rank < 0) {
-                        // dense node: y[r0 + i] += sum_j D[i, j] x[c0 + j]
-                        for (int i = lane; i < s; i += 32) {
-                            T acc[NR];
+            const T* Lm = pool + B.leaf_off + (size_t)li * leaf * leaf;
+            for (int c = g; c < leaf; c += KG) {
+                const T m = Lm[rr + (size_t)c * leaf];
 #pragma unroll
-                            for (int q = 0; q < NR; ++q) acc[q] = T(0);
-                            for (int j = 0; j < s; ++j) {
-                                const T m = d[i + (size_t)j * s];
-#pragma unroll
-                                for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[(c0 + j) * NR + q], acc[q]);
-                            }
-#pragma unroll
-                            for (int q = 0; q < NR; ++q) ys[(r0 + i) * NR + q] += acc[q];
-                        }
-                        continue;
-                    }
-                    const int rk = hn.rank;
-                    const T* U = d;
-                    const T* V = d + (size_t)s * rk;
-                    T* tw = ts + (size_t)warp * 64 * NR;
-                    // tw = V^T x[c0 : c0 + s]   (rk <= 64)
-                    for (int i = 0; i < rk; ++i) {
-                        T acc[NR];
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) acc[q] = T(0);
-                        for (int j = lane; j < s; j += 32) {
-                            const T m = V[j + (size_t)i * s];
-#pragma unroll
-                            for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[(c0 + j) * NR + q], acc[q]);
-                        }
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) {
-                            const T v = warp_sum(acc[q]);
-                            if (lane == 0) tw[i * NR + q] = v;
-                        }
-                    }
-                    __syncwarp();
-                    // y[r0 : r0 + s] += U tw
-                    for (int i = lane; i < s; i += 32) {
-                        T acc[NR];
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) acc[q] = T(0);
-                        for (int j = 0; j < rk; ++j) {
-                            const T m = U[i + (size_t)j * s];
-#pragma unroll
-                            for (int q = 0; q < NR; ++q) acc[q] = fma(m, tw[j * NR + q], acc[q]);
-                        }
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) ys[(r0 + i) * NR + q] += acc[q];
-                    }
-                    __syncwarp();
-                }
-                nb += nn;
-                __syncthreads();
+                for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[c * NR + q], acc[q]);
             }
-        }
-        for (int i = tid; i < b * NR; i += 256) {
-            const int r = i % b, q = i / b;
-            if (q < nq) {
-                T o = P.alpha * ys[r * NR + q];
-                if (P.cin) o += P.cin[r + (size_t)(q0 + q) * P.ldc];
-                P.out[r + (size_t)(q0 + q) * P.ldo] = o;
+            // tree levels
+            for (int l = 1; l <= L; ++l) {
+                const int s = b >> l, ni = R0 / s;
+                const HNode hn = nodes[B.node_base + (1 << l) - 2 + ni];
+                const int r0 = ni * s, c0 = (ni ^ 1) * s;
+                const T* d = pool + hn.off;
+                __syncthreads();
+                if (hn.rank < 0) {
+                    for (int i = tid; i < s * NR; i += 256) {
+                        const int c = i % s, q = i / s;
+                        xs[c * NR + q] = q < nq ? xval(P, t, c0 + c, q0 + q) : T(0);
+                    }
+                    __syncthreads();
+                    for (int c = g; c < s; c += KG) {
+                        const T m = d[(row - r0) + (size_t)c * s];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[c * NR + q], acc[q]);
+                    }
+                } else if (hn.rank > 0) {
+                    const int rk = hn.rank;
+                    const long long toff = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
+                    for (int i = tid; i < rk * NR; i += 256) {
+                        const int ii = i % rk, q = i / rk;
+                        xs[ii * NR + q] = q < nq ? tbuf[toff + ii + (size_t)(q0 + q) * rk] : T(0);
+                    }
+                    __syncthreads();
+                    for (int ii = g; ii < rk; ii += KG) {
+                        const T m = d[(row - r0) + (size_t)ii * s];
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[ii * NR + q], acc[q]);
+                    }
+                }
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NR; ++q) red[((size_t)g * RT + lr) * NR + q] = acc[q];
+        __syncthreads();
+        for (int i = tid; i < RT * NR; i += 256) {
+            const int r = i % RT, q = i / RT;
+            if (q < nq) {
+                T sum = T(0);
+                for (int gg = 0; gg < KG; ++gg) sum += red[((size_t)gg * RT + r) * NR + q];
+                T o = P.alpha * sum;
+                if (P.cin) o += P.cin[R0 + r + (size_t)(q0 + q) * P.ldc];
+                P.out[R0 + r + (size_t)(q0 + q) * P.ldo] = o;
+            }
+        }
     }
 }
 
 template <class T>
-cudaError_t hsweep(const HSweepProb<T>* probs, int nprob, const HBlk* blks, const HNode* nodes, const T* pool, int b,
-                   int leaf, int L, int nrhs, cudaStream_t s) {
+cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, const HTask* tasks, const int* alist,
+                   int a_off, int na, T* tbuf, const HBlk* blks, const HNode* nodes, const T* pool, int b, int leaf,
+                   int L, int nrhs, cudaStream_t s) {
     if (nprob <= 0 || nrhs <= 0) return cudaSuccess;
     const int NR = nrhs == 1 ? 1 : (nrhs <= 4 ? 4 : 8);
-    const size_t sm = ((size_t)2 * b * NR + (size_t)8 * 64 * NR) * sizeof(T);
+    // row tile: the largest power of two (<= 64) dividing the leaf, so that a
+    // tile lies inside one leaf and inside one node of every tree level
+    int RT = 1;
+    while (RT < 64 && leaf % (RT * 2) == 0) RT *= 2;
+    const size_t sm = ((size_t)std::max(b / 2, leaf) * NR + (size_t)256 * NR) * sizeof(T);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
-    if (NR == 1) {
-        cudaFuncSetAttribute(k_hsweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_hsweep<T, 1><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
-    } else if (NR == 4) {
-        cudaFuncSetAttribute(k_hsweep<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_hsweep<T, 4><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
-    } else {
-        cudaFuncSetAttribute(k_hsweep<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_hsweep<T, 8><<<nprob, 256, sm, s>>>(probs, blks, nodes, pool, b, leaf, L, nrhs);
+    const dim3 gb(b / RT, nprob);
+    const size_t smA = ((size_t)std::max(b / 2, 1) * NR + (size_t)8 * 64 * NR) * sizeof(T);
+    if (smA > 200 * 1024) return cudaErrorInvalidValue;
+#define ACR_HS_LAUNCH(NRV)                                                                                       \
+    {                                                                                                            \
+        if (na > 0) {                                                                                            \
+            cudaFuncSetAttribute(k_hnode_t<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);      \
+            k_hnode_t<T, NRV><<<na, 256, smA, s>>>(probs_all, tasks, alist + a_off, nodes, pool, b, nrhs, tbuf);  \
+            count_launches(1);                                                                                   \
+        }                                                                                                        \
+        cudaFuncSetAttribute(k_hrows<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
+        k_hrows<T, NRV><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf, L,    \
+                                            nrhs, RT);                                                           \
+        count_launches(1);                                                                                       \
     }
-    count_launches(1);
+    if (NR == 1) ACR_HS_LAUNCH(1)
+    else if (NR == 4) ACR_HS_LAUNCH(4)
+    else ACR_HS_LAUNCH(8)
+#undef ACR_HS_LAUNCH
     return cudaGetLastError();
 }
 
@@ -570,8 +639,8 @@ cudaError_t hsweep(const HSweepProb<T>* probs, int nprob, const HBlk* blks, cons
     template cudaError_t pack_nodes<T>(const HNode*, int, int, const T*, const T*, const T* const*, int, int, int, \
                                        T*, cudaStream_t);                                                         \
     template cudaError_t pack_leaves<T>(const T* const*, const long long*, int, int, int, T*, cudaStream_t);       \
-    template cudaError_t hsweep<T>(const HSweepProb<T>*, int, const HBlk*, const HNode*, const T*, int, int, int,  \
-                                   int, cudaStream_t);
+    template cudaError_t hsweep<T>(const HSweepProb<T>*, int, int, const HTask*, const int*, int, int, T*,        \
+                                   const HBlk*, const HNode*, const T*, int, int, int, int, cudaStream_t);
 ACR_HODLR_INST(float)
 ACR_HODLR_INST(double)
 
