@@ -314,187 +314,14 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     if (tid == 0 && first_bad && info[blockIdx.x] == 0) info[blockIdx.x] = first_bad;
 }
 
-template <class T, int NT, int JT>
-__global__ void __launch_bounds__(NT) k_gj_update(T* __restrict__ mats, int b, int k0, int kb,
-                                                  const int* __restrict__ pivs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // stash: (2*kb) x JT values of displaced rows; T rows (the panel's pivot
-    // rows after interchange) occupy slots [0, kb)
-    T* stash = reinterpret_cast<T*>(smem_raw);
-    int* perm = reinterpret_cast<int*>(stash + 2 * kb * JT);   // b
-    int* slot = perm + b;                                      // b
-    int* list = slot + b;                                      // kb
-    __shared__ int s_cnt;
-    T* G = mats + (size_t)blockIdx.y * b * b;
-    const int* piv = pivs + (size_t)blockIdx.y * b;
-    const int tid = threadIdx.x;
-    const int nJ = b - kb;
-    const int j0 = blockIdx.x * JT;
-    for (int r = tid; r < b; r += NT) { perm[r] = r; slot[r] = -1; }
-    __syncthreads();
-    if (tid == 0) {
-        for (int kk = 0; kk < kb; ++kk) {
-            const int k = k0 + kk, p = piv[k];
-            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
-            slot[k] = kk;
-        }
-        int cnt = 0;
-        for (int kk = 0; kk < kb; ++kk) {
-            const int p = piv[k0 + kk];
-            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
-        }
-        s_cnt = cnt;
-    }
-    __syncthreads();
-    const int ns = kb + s_cnt;
-    for (int i = tid; i < ns * JT; i += NT) {
-        const int s = i % ns, j = i / ns;
-        const int jc = j0 + j;
-        T v = T(0);
-        if (jc < nJ) {
-            const int c = jc < k0 ? jc : jc + kb;
-            const int r = s < kb ? k0 + s : list[s - kb];
-            v = G[perm[r] + (size_t)c * b];
-        }
-        stash[s + j * 2 * kb] = v;
-    }
-    __syncthreads();
-    int ncol = nJ - j0;
-    if (ncol > JT) ncol = JT;
-    for (int r = tid; r < b; r += NT) {
-        T acc[JT];
-        const int sl = slot[r];
-#pragma unroll
-        for (int j = 0; j < JT; ++j) {
-            const int jc = j0 + j;
-            const int c = jc < k0 ? jc : jc + kb;
-            T base = T(0);
-            if (j < ncol) base = (sl < 0) ? G[r + (size_t)c * b] : (sl < kb ? T(0) : stash[sl + j * 2 * kb]);
-            acc[j] = base;
-        }
-        for (int kk = 0; kk < kb; ++kk) {
-            const T pv = G[r + (size_t)(k0 + kk) * b];
-#pragma unroll
-            for (int j = 0; j < JT; ++j) acc[j] += pv * stash[kk + j * 2 * kb];
-        }
-#pragma unroll
-        for (int j = 0; j < JT; ++j) {
-            if (j < ncol) {
-                const int jc = j0 + j;
-                const int c = jc < k0 ? jc : jc + kb;
-                G[r + (size_t)c * b] = acc[j];
-            }
-        }
-    }
-}
-
-// Tiled update step: the same arithmetic as k_gj_update, organised as a GEMM
-// with K = kb.  One CTA owns a strip of BN columns of J (all rows, so the
-// in-place row interchange is race-free: the displaced rows of the strip are
-// read into shared memory first).  Row tiles of BM rows are streamed:
-//   acc = Panel[rows, K] * (P M)[K, strip]          (BM x BN, TM x TN per thread)
-//   M[r, strip] = base(r) + acc,  base = 0 (r in K) | (P M)[r, strip]
-template <class T, int BM, int BN, int TM, int TN, int KBMAX>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_gj_update_tiled(T* __restrict__ mats, int b, int k0, int kb, const int* __restrict__ pivs) {
-    constexpr int RY = BM / TM, RX = BN / TN, NT = RY * RX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* stash = reinterpret_cast<T*>(smem_raw);           // [2*KBMAX][BN]: slot s, column j
-    T* Ps = stash + 2 * KBMAX * BN;                       // [KBMAX][BM]: panel tile, k-major
-    int* perm = reinterpret_cast<int*>(Ps + KBMAX * BM);  // b
-    int* slot = perm + b;                                 // b
-    int* list = slot + b;                                 // KBMAX
-    __shared__ int s_cnt;
-    T* G = mats + (size_t)blockIdx.y * b * b;
-    const int* piv = pivs + (size_t)blockIdx.y * b;
-    const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
-    const int nJ = b - kb;
-    const int j0 = blockIdx.x * BN;
-    for (int r = tid; r < b; r += NT) { perm[r] = r; slot[r] = -1; }
-    __syncthreads();
-    if (tid == 0) {
-        for (int kk = 0; kk < kb; ++kk) {
-            const int k = k0 + kk, p = piv[k];
-            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
-            slot[k] = kk;
-        }
-        int cnt = 0;
-        for (int kk = 0; kk < kb; ++kk) {
-            const int p = piv[k0 + kk];
-            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
-        }
-        s_cnt = cnt;
-    }
-    __syncthreads();
-    const int ns = kb + s_cnt;
-    // displaced rows of this strip (slots < kb are the interchanged pivot rows)
-    for (int i = tid; i < ns * BN; i += NT) {
-        const int s = i / BN, j = i % BN;
-        const int jc = j0 + j;
-        T v = T(0);
-        if (jc < nJ) {
-            const int c = jc < k0 ? jc : jc + kb;
-            const int r = s < kb ? k0 + s : list[s - kb];
-            v = G[perm[r] + (size_t)c * b];
-        }
-        stash[s * BN + j] = v;
-    }
-    int cidx[TN];
-    bool cok[TN];
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-        const int jc = j0 + tx + j * RX;
-        cok[j] = jc < nJ;
-        cidx[j] = jc < k0 ? jc : jc + kb;
-    }
-    for (int row0 = 0; row0 < b; row0 += BM) {
-        __syncthreads();  // stash written / previous Ps reads done
-        for (int i = tid; i < kb * BM; i += NT) {
-            const int r = i % BM, k = i / BM;
-            const int gr = row0 + r;
-            Ps[k * BM + r] = (gr < b) ? G[gr + (size_t)(k0 + k) * b] : T(0);
-        }
-        __syncthreads();
-        T acc[TM][TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-        for (int k = 0; k < kb; ++k) {
-            T af[TM], bf[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) af[i] = Ps[k * BM + ty + i * RY];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) bf[j] = stash[k * BN + tx + j * RX];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(af[i], bf[j], acc[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            const int r = row0 + ty + i * RY;
-            if (r >= b) continue;
-            const int sl = slot[r];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                if (!cok[j]) continue;
-                const size_t o = r + (size_t)cidx[j] * b;
-                const T base = (sl < 0) ? G[o] : (sl < kb ? T(0) : stash[sl * BN + tx + j * RX]);
-                G[o] = base + acc[i][j];
-            }
-        }
-    }
-}
-
 // Two-kernel update for full parallelism over (row tile, column tile, block).
 // gather: the rows that the panel's interchanges move (the kb pivot rows K
 // and the rows they were swapped with) are copied, after interchange, to a
 // stash (slot s, all b columns); slot map: -1 (row unchanged), s < kb (row in
 // K: base 0, stash row s is (P M)[K]), s >= kb (displaced row: base = stash).
 template <class T>
-__global__ void k_gj_gather(const T* __restrict__ mats, int b, int k0, int kb, const int* __restrict__ pivs,
-                            T* __restrict__ stash, int* __restrict__ slotmap) {
+__global__ void k_gj_gather(const T* __restrict__ mats, int b, int k0, int kb, int colA, int colB,
+                            const int* __restrict__ pivs, T* __restrict__ stash, int* __restrict__ slotmap) {
     extern __shared__ int sh_i[];
     int* perm = sh_i;        // b
     int* slot = perm + b;    // b
@@ -522,10 +349,10 @@ __global__ void k_gj_gather(const T* __restrict__ mats, int b, int k0, int kb, c
     const int ns = kb + s_cnt;
     if (blockIdx.x == 0)
         for (int r = threadIdx.x; r < b; r += blockDim.x) slotmap[(size_t)blockIdx.y * b + r] = slot[r];
-    const int c0 = blockIdx.x * 64;
+    const int c0 = colA + blockIdx.x * 64;  // this CTA's columns of [colA, colB)
     for (int i = threadIdx.x; i < ns * 64; i += blockDim.x) {
         const int s = i % ns, j = i / ns, c = c0 + j;
-        if (c >= b) continue;
+        if (c >= colB) continue;
         const int r = s < kb ? k0 + s : list[s - kb];
         st[(size_t)s * b + c] = G[perm[r] + (size_t)c * b];
     }
@@ -534,7 +361,7 @@ __global__ void k_gj_gather(const T* __restrict__ mats, int b, int k0, int kb, c
 // update: acc = Panel[rows, K] * stash[0:kb, cols] over the columns outside K.
 template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict__ stash,
+k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, int colA, int colB, const T* __restrict__ stash,
                 const int* __restrict__ slotmap, int tiles_m) {
     constexpr int RY = BM / TM, RX = BN / TN, NT = RY * RX;
     __shared__ T As[BK][BM];
@@ -542,7 +369,7 @@ k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
     T* G = mats + (size_t)blockIdx.y * b * b;
     const T* st = stash + (size_t)blockIdx.y * 2 * kb * b;
     const int* slot = slotmap + (size_t)blockIdx.y * b;
-    const int nJ = b - kb;
+    const int nJ = (colB - colA) - kb;  // columns of [colA, colB) outside the panel
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
     const int row0 = tm * BM, j0 = tn * BN;
     const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
@@ -560,7 +387,7 @@ k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
         for (int i = tid; i < BK * BN; i += NT) {
             const int j = i % BN, k = i / BN;
             const int jc = j0 + j;
-            const int c = jc < k0 ? jc : jc + kb;
+            const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
             Bs[k][j] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
         }
         __syncthreads();
@@ -582,7 +409,7 @@ k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
     for (int j = 0; j < TN; ++j) {
         const int jc = j0 + tx + j * RX;
         if (jc >= nJ) continue;
-        const int c = jc < k0 ? jc : jc + kb;
+        const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int r = row0 + ty + i * RY;
@@ -600,7 +427,7 @@ k_gj_update_par(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
 // column).  Tile BM x BN, TN columns per thread.
 template <class T, int V, int BM, int BN, int BK, int TN>
 __global__ void __launch_bounds__((BM / V) * (BN / TN))
-k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict__ stash,
+k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, int colA, int colB, const T* __restrict__ stash,
                 const int* __restrict__ slotmap, int tiles_m) {
     using VT = typename VecT<T, V>::type;
     constexpr int RY = BM / V, RX = BN / TN, NT = RY * RX;
@@ -609,7 +436,7 @@ k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
     T* G = mats + (size_t)blockIdx.y * b * b;
     const T* st = stash + (size_t)blockIdx.y * 2 * kb * b;
     const int* slot = slotmap + (size_t)blockIdx.y * b;
-    const int nJ = b - kb;
+    const int nJ = (colB - colA) - kb;  // columns of [colA, colB) outside the panel
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
     const int row0 = tm * BM, j0 = tn * BN;
     const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
@@ -628,7 +455,7 @@ k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
         for (int i = tid; i < BK * BN; i += NT) {
             const int j = i % BN, k = i / BN;
             const int jc = j0 + j;
-            const int c = jc < k0 ? jc : jc + kb;
+            const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
             Bs[k][j] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
         }
         __syncthreads();
@@ -659,7 +486,7 @@ k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, const T* __restrict
     for (int j = 0; j < TN; ++j) {
         const int jc = j0 + tx + j * RX;
         if (jc >= nJ) continue;
-        const int c = jc < k0 ? jc : jc + kb;
+        const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
         T* gp = G + rbase + (size_t)c * b;
         if (plain) {
             VT v = *reinterpret_cast<const VT*>(gp);
@@ -729,6 +556,70 @@ static size_t gj_small_smem(int b) {
     return (size_t)(b + 1) * b * sizeof(T) + 2 * (size_t)b * sizeof(int);
 }
 
+// Outer panel width of the two-level blocked inversion.
+template <class T>
+static int gj_outer_width(int b) {
+    const int KB = sizeof(T) == 8 ? 16 : 32;
+    return b >= 4 * 128 ? 128 : (b >= 4 * 64 ? 64 : KB);
+}
+
+// Two-level blocked Gauss-Jordan: inner panels of KB columns (register
+// kernel) update only their outer panel of KO columns; after the outer panel
+// is done, one rank-KO update (the same identity with panel width KO) brings
+// every other column up to date.  Each column outside the outer panel is read
+// and written once per outer panel instead of once per inner panel.
+template <class T>
+static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv, T* amax, T* stash, int* slotmap,
+                              cudaStream_t s) {
+    constexpr int KB = sizeof(T) == 8 ? 16 : 32;
+    const int KO = gj_outer_width<T>(b);
+    cudaMemsetAsync(amax, 0, sizeof(T) * count, s);
+    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
+    count_launches(1);
+    const size_t psmem = (size_t)b * KB * sizeof(T);
+    auto kp = k_gj_panel<T, 512>;
+    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    const int rpt = (b + 511) / 512;
+    constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
+    // rank-kw update of the columns [cA, cB) outside [k0, k0 + kw)
+    auto update = [&](int k0, int kw, int cA, int cB) {
+        const int nJ = (cB - cA) - kw;
+        if (nJ <= 0) return;
+        k_gj_gather<T><<<dim3((cB - cA + 63) / 64, count), 256, (2 * (size_t)b + kw) * sizeof(int), s>>>(
+            mats, b, k0, kw, cA, cB, ws_piv, stash, slotmap);
+        count_launches(1);
+        const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
+        if (b % (16 / (int)sizeof(T)) == 0) {
+            constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
+            k_gj_update_vec<T, VV, BMU, BMU, 8, TNV><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                mats, b, k0, kw, cA, cB, stash, slotmap, tmu);
+        } else {
+            k_gj_update_par<T, BMU, BMU, 8, TMU, TMU><<<dim3(tmu * tnu, count), 256, 0, s>>>(
+                mats, b, k0, kw, cA, cB, stash, slotmap, tmu);
+        }
+        count_launches(1);
+    };
+    for (int K0 = 0; K0 < b; K0 += KO) {
+        const int KOi = (b - K0) < KO ? (b - K0) : KO;
+        for (int k0 = K0; k0 < K0 + KOi; k0 += KB) {
+            const int kbi = (K0 + KOi - k0) < KB ? (K0 + KOi - k0) : KB;
+            if (kbi == KB && rpt <= 2) {  // panel rows fit in registers (<= 2 per thread)
+                if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+                else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+            } else {
+                kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
+            }
+            count_launches(1);
+            update(k0, kbi, K0, K0 + KOi);  // inside the outer panel
+        }
+        update(K0, KOi, 0, b);  // everything else, once per outer panel
+    }
+    dim3 gu((b + 255) / 256, count);
+    k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
@@ -741,69 +632,22 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
         count_launches(1);
         return cudaGetLastError();
     }
-    // blocked path
-    const int kb = sizeof(T) == 8 ? 16 : 32;
+    // blocked path: temporaries from the stream-ordered pool
+    const int KO = gj_outer_width<T>(b);
     T* amax = nullptr;
     cudaError_t e = cudaMallocAsync(&amax, sizeof(T) * count, s);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(amax, 0, sizeof(T) * count, s);
-    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
-    count_launches(1);
-    constexpr int JT = 16;
-    constexpr int KB = sizeof(T) == 8 ? 16 : 32;
-    const size_t psmem = (size_t)b * kb * sizeof(T);
-    const size_t usmem = (size_t)2 * kb * JT * sizeof(T) + (2 * (size_t)b + kb) * sizeof(int);
-    auto kp = k_gj_panel<T, 512>;
-    auto ku = k_gj_update<T, 256, JT>;
-    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
-    const int rpt = (b + 511) / 512;
-    // stash of interchanged rows + slot map for the parallel update
     T* stash = nullptr;
-    int* slotmap = nullptr;
-    if (cudaMallocAsync(&stash, sizeof(T) * (size_t)count * 2 * kb * b + sizeof(int) * (size_t)count * b, s) ==
-        cudaSuccess)
-        slotmap = reinterpret_cast<int*>(stash + (size_t)count * 2 * kb * b);
-    else
-        cudaGetLastError(), stash = nullptr;
-    for (int k0 = 0; k0 < b; k0 += kb) {
-        const int kbi = (b - k0) < kb ? (b - k0) : kb;
-        if (kbi == KB && rpt <= 2) {  // panel rows fit in registers (<= 2 per thread)
-            if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-            else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-        } else {
-            kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
-        }
-        count_launches(1);
-        const int nJ = b - kbi;
-        if (nJ > 0) {
-            if (b >= 128 && stash) {
-                constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
-                k_gj_gather<T><<<dim3((b + 63) / 64, count), 256, (2 * (size_t)b + kbi) * sizeof(int), s>>>(
-                    mats, b, k0, kbi, ws_piv, stash, slotmap);
-                count_launches(1);
-                const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
-                if (b % (16 / (int)sizeof(T)) == 0) {
-                    constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
-                    k_gj_update_vec<T, VV, BMU, BMU, 8, TNV><<<dim3(tmu * tnu, count), 256, 0, s>>>(
-                        mats, b, k0, kbi, stash, slotmap, tmu);
-                } else {
-                    k_gj_update_par<T, BMU, BMU, 8, TMU, TMU><<<dim3(tmu * tnu, count), 256, 0, s>>>(
-                        mats, b, k0, kbi, stash, slotmap, tmu);
-                }
-            } else {
-                dim3 g((nJ + JT - 1) / JT, count);
-                ku<<<g, 256, usmem, s>>>(mats, b, k0, kbi, ws_piv);
-            }
-            count_launches(1);
-        }
+    e = cudaMallocAsync(&stash, sizeof(T) * (size_t)count * 2 * KO * b + sizeof(int) * (size_t)count * b, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(amax, s);
+        return e;
     }
-    dim3 gu((b + 255) / 256, count);
-    k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
-    count_launches(1);
+    int* slotmap = reinterpret_cast<int*>(stash + (size_t)count * 2 * KO * b);
+    e = gj_blocked<T>(mats, b, count, info, ws_piv, amax, stash, slotmap, s);
     cudaFreeAsync(amax, s);
-    if (stash) cudaFreeAsync(stash, s);
-    return cudaGetLastError();
+    cudaFreeAsync(stash, s);
+    return e;
 }
 
 // Scratch layout of gj_inverse_scratch (each part 256-byte aligned):
@@ -814,9 +658,9 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 template <class T>
 size_t gj_scratch_bytes(int b, int count) {
     if (count <= 0 || gj_small_smem<T>(b) <= 200 * 1024) return 0;
-    const int kb = sizeof(T) == 8 ? 16 : 32;
+    const int KO = gj_outer_width<T>(b);
     return al256(sizeof(int) * (size_t)count * b) + al256(sizeof(T) * (size_t)count) +
-           al256(sizeof(T) * (size_t)count * 2 * kb * b) + al256(sizeof(int) * (size_t)count * b);
+           al256(sizeof(T) * (size_t)count * 2 * KO * b) + al256(sizeof(int) * (size_t)count * b);
 }
 
 // The same batched inversion as gj_inverse, with every temporary taken from
@@ -836,54 +680,16 @@ cudaError_t gj_inverse_scratch(T* mats, int b, int count, int* info, void* scrat
         count_launches(1);
         return cudaGetLastError();
     }
-    constexpr int KB = sizeof(T) == 8 ? 16 : 32;
-    const int kb = KB;
+    const int KO = gj_outer_width<T>(b);
     char* p = static_cast<char*>(scratch);
     int* ws_piv = reinterpret_cast<int*>(p);
     p += al256(sizeof(int) * (size_t)count * b);
     T* amax = reinterpret_cast<T*>(p);
     p += al256(sizeof(T) * (size_t)count);
     T* stash = reinterpret_cast<T*>(p);
-    p += al256(sizeof(T) * (size_t)count * 2 * kb * b);
+    p += al256(sizeof(T) * (size_t)count * 2 * KO * b);
     int* slotmap = reinterpret_cast<int*>(p);
-    cudaMemsetAsync(amax, 0, sizeof(T) * count, s);  // the max reduction accumulates into zeros
-    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
-    count_launches(1);
-    constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
-    const size_t psmem = (size_t)b * kb * sizeof(T);
-    auto kp = k_gj_panel<T, 512>;
-    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    const int rpt = (b + 511) / 512;
-    for (int k0 = 0; k0 < b; k0 += kb) {
-        const int kbi = (b - k0) < kb ? (b - k0) : kb;
-        if (kbi == KB && rpt <= 2) {
-            if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-            else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-        } else {
-            kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
-        }
-        count_launches(1);
-        const int nJ = b - kbi;
-        if (nJ > 0) {
-            k_gj_gather<T><<<dim3((b + 63) / 64, count), 256, (2 * (size_t)b + kbi) * sizeof(int), s>>>(
-                mats, b, k0, kbi, ws_piv, stash, slotmap);
-            count_launches(1);
-            const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
-            if (b % (16 / (int)sizeof(T)) == 0) {
-                constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
-                k_gj_update_vec<T, VV, BMU, BMU, 8, TNV><<<dim3(tmu * tnu, count), 256, 0, s>>>(
-                    mats, b, k0, kbi, stash, slotmap, tmu);
-            } else {
-                k_gj_update_par<T, BMU, BMU, 8, TMU, TMU><<<dim3(tmu * tnu, count), 256, 0, s>>>(
-                    mats, b, k0, kbi, stash, slotmap, tmu);
-            }
-            count_launches(1);
-        }
-    }
-    dim3 gu((b + 255) / 256, count);
-    k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
-    count_launches(1);
-    return cudaGetLastError();
+    return gj_blocked<T>(mats, b, count, info, ws_piv, amax, stash, slotmap, s);
 }
 template size_t gj_scratch_bytes<double>(int, int);
 template size_t gj_scratch_bytes<float>(int, int);
