@@ -155,14 +155,33 @@ def measured_peaks():
 
 
 def traffic_record(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one
-    exists for the current build of that kernel."""
+    """The committed ncu DRAM-traffic record of `kernel`, or None when there is
+    none or the kernel's source changed since the counters were taken."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel)
+        rec = json.load(open(path)).get("k_" + kernel)
     except (OSError, ValueError):
         return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1604_00617_gb300", "csrc", "k_tc.cu")
+    try:
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec.get("source_sha1"):
+            return None
+    except OSError:
+        return None
     return rec
+
+
+def scaled_traffic(rec, flops_per_launch, b):
+    """Traffic of an average launch: the captured DRAM bytes per output element
+    of a one-term b_cap x b_cap product, times the output elements of the
+    average launch (its algorithmic flops / (2 b^3) one-term products of b^2
+    elements)."""
+    if not rec:
+        return None
+    return rec["bytes_per_output_element"] * (flops_per_launch / (2.0 * b ** 3)) * b * b
 
 
 # ----------------------------------------------------------------------------
@@ -314,10 +333,12 @@ def run_ours(args):
     else:
         peak, src = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 2 FP64 FMA/clk x 2 x max SM clock"
         bound = "alu"
-    tr = traffic_record(kernel)
+    tr = traffic_record(kernel) if kernel == "gemm_tc" else None
+    fpl = last["gemm_flops"] / max(1, last["gemm_launches"])
     roof = {"kernel": kernel, "bound": bound, "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
             "frac": gemm_tflops / peak, "peak_source": src,
-            "traffic": tr.get("bytes_per_launch") if tr else None,
+            "traffic": scaled_traffic(tr, fpl, P.b),
+            "traffic_source": (tr["capture"] + "; scaled by output elements to the average launch") if tr else None,
             "algorithmic_per_launch": last["gemm_flops"] / max(1, last["gemm_launches"]),
             "launch_ms": last["gemm_ms"] / max(1, last["gemm_launches"])}
 
