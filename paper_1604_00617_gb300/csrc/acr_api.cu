@@ -1234,6 +1234,11 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
         if ((st = P.apply(f, x))) return st;
         iters = 1;
     }
+    // A column whose residual has reached tol is frozen: later corrections
+    // leave it untouched, so every column follows the iteration it would
+    // follow alone whatever other columns share the call (the kernels'
+    // per-column arithmetic does not depend on nrhs).
+    std::vector<char> frozen(nrhs, 0);
     auto check = [&](bool& conv) -> int {
         int e = op.res();
         if (e) return e;
@@ -1243,7 +1248,8 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
         conv = true;
         for (int q = 0; q < nrhs; ++q) {
             rel[q] = fn2[q] > 0 ? std::sqrt(hs[q] / fn2[q]) : std::sqrt(hs[q]);
-            if (!(rel[q] <= tol)) conv = false;
+            if (rel[q] <= tol) frozen[q] = 1;
+            if (!frozen[q]) conv = false;
         }
         return ACR_OK;
     };
@@ -1251,10 +1257,13 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
     if ((st = check(conv))) return st;
     if (conv || method == ACR_REFINE_NONE) return conv ? ACR_OK : fail(ACR_ERR_NOT_CONVERGED, "residual %g above ir_tol %g and refinement is off", *std::max_element(rel.begin(), rel.end()), tol);
     if (method == ACR_REFINE_IR) {
+        std::vector<double> mask(nrhs);
         while (iters < maxit && !conv) {
             if ((st = P.apply(r.as<double>(), zb.as<double>()))) return st;
             ++iters;
-            CK(add_d2d(x, zb.as<double>(), NQ, s));
+            for (int q = 0; q < nrhs; ++q) mask[q] = frozen[q] ? 0.0 : 1.0;
+            CK(cudaMemcpyAsync(coef.p, mask.data(), nrhs * 8, cudaMemcpyHostToDevice, s));
+            CK(multi_axpy(x, zb.as<double>(), 1, coef.as<double>(), N, nrhs, s));
             if ((st = check(conv))) return st;
         }
     } else {
@@ -1271,8 +1280,11 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
         while (iters < maxit && !conv) {
             std::fill(H.begin(), H.end(), 0.0);
             std::fill(g.begin(), g.end(), 0.0);
+            // a frozen column restarts from a zero vector: its Krylov space
+            // stays {0}, its y is 0 and x keeps its value
+            std::vector<int> jdq(nrhs, 0);
             for (int q = 0; q < nrhs; ++q) {
-                const double beta = std::sqrt(hs[q]);
+                const double beta = frozen[q] ? 0.0 : std::sqrt(hs[q]);
                 g[(size_t)q * (m + 1)] = beta;
                 sc[q] = beta > 0 ? 1.0 / beta : 0.0;
             }
@@ -1324,7 +1336,10 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
                     gq[j + 1] = -sv * gq[j];
                     gq[j] = c * gq[j];
                     const double est = fn2[q] > 0 ? std::fabs(gq[j + 1]) / std::sqrt(fn2[q]) : std::fabs(gq[j + 1]);
-                    if (!(est <= 0.5 * tol)) all = false;
+                    // a column stops its cycle at its first step below the
+                    // target; later steps do not enter its update
+                    if (jdq[q] == 0 && (frozen[q] || est <= 0.5 * tol)) jdq[q] = j + 1;
+                    if (jdq[q] == 0) all = false;
                 }
                 CK(cudaMemcpyAsync(coef.p, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, s));
                 CK(col_scale(Vp + (size_t)(j + 1) * NQ, w, coef.as<double>(), N, nrhs, s));
@@ -1334,9 +1349,11 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
             // y = R^-1 g per column, x += Z y
             for (int q = 0; q < nrhs; ++q) {
                 const double* gq = &g[(size_t)q * (m + 1)];
-                for (int i = jd - 1; i >= 0; --i) {
+                const int jq = jdq[q] > 0 ? jdq[q] : jd;
+                for (int i = jd - 1; i >= jq; --i) y[(size_t)i * nrhs + q] = 0.0;
+                for (int i = jq - 1; i >= 0; --i) {
                     double t = gq[i];
-                    for (int k = i + 1; k < jd; ++k) t -= Hq(q, i, k) * y[(size_t)k * nrhs + q];
+                    for (int k = i + 1; k < jq; ++k) t -= Hq(q, i, k) * y[(size_t)k * nrhs + q];
                     const double d = Hq(q, i, i);
                     y[(size_t)i * nrhs + q] = std::fabs(d) > 0 ? t / d : 0.0;
                 }

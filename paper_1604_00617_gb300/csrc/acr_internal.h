@@ -13,6 +13,12 @@ namespace acr {
 long long launch_count();
 void count_launches(int k);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The limit only ever grows, under a lock, so a launch by one
+// host thread is never undercut by another thread setting a smaller limit for
+// the same kernel between its call here and its launch.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+
 // One batched block product: out = beta * cin + alpha * sum_t a[t] * bm[t],
 // every operand a blksz x blksz column-major block (leading dimension blksz).
 // A NULL a[t] drops term t; a NULL cin means beta is ignored.

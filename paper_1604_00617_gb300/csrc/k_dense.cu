@@ -16,6 +16,8 @@
 #include <cfloat>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "acr_internal.h"
 
@@ -24,6 +26,19 @@ namespace acr {
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
 void count_launches(int k) { g_launches.fetch_add(k); }
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 template <class T> struct Lim;
 template <> struct Lim<float> { static __device__ __forceinline__ float eps() { return FLT_EPSILON; } };
@@ -578,7 +593,7 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
     count_launches(1);
     const size_t psmem = (size_t)b * KB * sizeof(T);
     auto kp = k_gj_panel<T, 512>;
-    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    ensure_smem((const void*)kp, psmem);
     const int rpt = (b + 511) / 512;
     constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
     // rank-kw update of the columns [cA, cB) outside [k0, k0 + kw)
@@ -627,7 +642,7 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
     const size_t small = gj_small_smem<T>(b);
     if (small <= 200 * 1024) {
         auto kern = k_gj_small<T, 256>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
+        ensure_smem((const void*)kern, small);
         kern<<<count, 256, small, s>>>(mats, b, info);
         count_launches(1);
         return cudaGetLastError();
@@ -675,7 +690,7 @@ cudaError_t gj_inverse_scratch(T* mats, int b, int count, int* info, void* scrat
     const size_t small = gj_small_smem<T>(b);
     if (small <= 200 * 1024) {
         auto kern = k_gj_small<T, 256>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
+        ensure_smem((const void*)kern, small);
         kern<<<count, 256, small, s>>>(mats, b, info);
         count_launches(1);
         return cudaGetLastError();
@@ -1024,15 +1039,15 @@ cudaError_t sweep_batched(const SweepProb<T>* d_probs, int nprob, int b, int nrh
         dim3 g(rtiles, nprob, nsplit);
         if (NRv == 1) {
             auto k = k_sweep_vec<T, V, 1, RG, KG>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            ensure_smem((const void*)k, vsm);
             k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
         } else if (NRv == 4) {
             auto k = k_sweep_vec<T, V, 4, RG, KG>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            ensure_smem((const void*)k, vsm);
             k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
         } else {
             auto k = k_sweep_vec<T, V, 8, RG, KG>;
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+            ensure_smem((const void*)k, vsm);
             k<<<g, RG * KG, vsm, s>>>(d_probs, b, nrhs, part);
         }
         count_launches(1);

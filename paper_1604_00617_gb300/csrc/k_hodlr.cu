@@ -340,7 +340,7 @@ cudaError_t node_svd(const T* Y, T* U, T* sig, int nnodes, int s, int k, cudaStr
     const int kz = node_svd_kz<T>(s, k);
     if (kz == 0) return cudaErrorInvalidValue;
     const size_t sm = node_svd_smem<T>(s, k, kz);
-    cudaFuncSetAttribute(k_node_svd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_smem((const void*)k_node_svd<T>, sm);
     int done = 0;
     while (done < nnodes) {
         const int cnt = std::min(nnodes - done, 1 << 30);
@@ -614,11 +614,11 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
     {                                                                                                            \
         if (na > 0) {                                                                                            \
-            cudaFuncSetAttribute(k_hnode_t<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);      \
+            ensure_smem((const void*)k_hnode_t<T, NRV>, smA);                                                  \
             k_hnode_t<T, NRV><<<na, 256, smA, s>>>(probs_all, tasks, alist + a_off, nodes, pool, b, nrhs, tbuf);  \
             count_launches(1);                                                                                   \
         }                                                                                                        \
-        cudaFuncSetAttribute(k_hrows<T, NRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);            \
+        ensure_smem((const void*)k_hrows<T, NRV>, sm);                                                         \
         k_hrows<T, NRV><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf, L,    \
                                             nrhs, RT);                                                           \
         count_launches(1);                                                                                       \

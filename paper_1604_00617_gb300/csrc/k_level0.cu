@@ -82,7 +82,7 @@ cudaError_t tridiag_inverse(const double* Dband, int n, int b, T* dinv, int* inf
     dim3 g((b + 127) / 128, ne);
     const size_t sm = 3 * (size_t)b * sizeof(double) + 2 * (size_t)b * sizeof(T);
     if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_tridiag_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        ensure_smem((const void*)k_tridiag_inv<T>, sm);
     k_tridiag_inv<T><<<g, 128, sm, s>>>(Dband, n, b, dinv, info);
     count_launches(1);
     return cudaGetLastError();

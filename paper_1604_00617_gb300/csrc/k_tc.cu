@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 
@@ -292,9 +293,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
+    // looked up once; every thread sees the final value (solves and factors
+    // may run concurrently from several host threads)
+    static std::once_flag once;
     static EncodeTiledFn fn = nullptr;
-    static std::atomic<int> tried{0};
-    if (!fn && !tried.exchange(1)) {
+    std::call_once(once, [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
@@ -303,7 +306,7 @@ static EncodeTiledFn encode_fn() {
             fn = reinterpret_cast<EncodeTiledFn>(p);
         else
             cudaGetLastError();
-    }
+    });
     return fn;
 }
 
@@ -329,9 +332,7 @@ size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
 cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s) {
     if (nprob <= 0) return cudaSuccess;
-    static std::atomic<int> attr_set{0};
-    if (!attr_set.exchange(1))
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    ensure_smem((const void*)k_gemm_tc, SMEM_BYTES);
     const int tiles_m = b / BM, tiles_n = b / BN;
     dim3 g(tiles_m * tiles_n, nprob);
     k_gemm_tc<<<g, NTHREADS, SMEM_BYTES, s>>>(d_probs, static_cast<const CUtensorMap*>(d_maps), b, tiles_m, d_err);

@@ -1,0 +1,179 @@
+"""Host-side tests of the serving loop's scheduling: admission under the
+memory budget, continuous batching, right-hand-side coalescing and failure
+propagation, with the CUDA library replaced by a fake that sleeps."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1604_00617_gb300 import _lib as acr
+from paper_1604_00617_gb300 import serving
+
+
+class FakeStream:
+    cuda_stream = 0
+
+
+class FakeLib:
+    """Factor and solve calls that take `tf` / `ts` seconds; a solve returns
+    2 * B; systems whose block count is in `fail` fail to factor."""
+
+    def __init__(self, tf=0.05, ts=0.01, fail=(), held=1 << 20):
+        self.tf, self.ts, self.fail, self.held = tf, ts, set(fail), held
+        self.lock = threading.Lock()
+        self.live = 0
+        self.max_live = 0
+        self.solve_calls = []   # (system id, nrhs)
+        self.freed = []
+
+    def acr_default_opts(self):
+        return acr.acr_default_opts()
+
+    def _enter(self):
+        with self.lock:
+            self.live += 1
+            self.max_live = max(self.max_live, self.live)
+
+    def _leave(self):
+        with self.lock:
+            self.live -= 1
+
+    def acr_factor_ex(self, nblk, blksz, a, D3, c, tol, o):
+        self._enter()
+        time.sleep(self.tf)
+        self._leave()
+        if nblk in self.fail:
+            raise acr.AcrError(acr.ACR_ERR_SINGULAR, "planted failure")
+        return {"id": int(a[0]), "n": nblk}
+
+    def acr_stats(self, h):
+        return {"factor_bytes": self.held, "operator_bytes": 0}
+
+    def acr_solve_ex(self, h, B, nrhs):
+        self._enter()
+        with self.lock:
+            self.solve_calls.append((h["id"], nrhs))
+        time.sleep(self.ts)
+        B *= 2.0
+        self._leave()
+        return np.zeros(nrhs), 1
+
+    def acr_free(self, h):
+        with self.lock:
+            self.freed.append(h["id"])
+
+
+def _system(rid, t, n, nsolve, tag=None):
+    a = np.full(n * n, float(rid if tag is None else tag))
+    return serving.SystemRequest(rid, t, n, n, a, np.zeros(3 * n * n), np.zeros(n * n), nsolve, 0.0, 0, "x")
+
+
+def _stream(spec, seed=0):
+    """spec: list of (arrival, n, solve arrivals) -> events."""
+    rng = np.random.default_rng(seed)
+    ev, rid = [], 0
+    for t, n, solves in spec:
+        sid = rid
+        ev.append((t, _system(sid, t, n, len(solves))))
+        rid += 1
+        for ts in solves:
+            ev.append((ts, serving.SolveRequest(rid, sid, ts, rng.uniform(-1, 1, n * n))))
+            rid += 1
+    return ev
+
+
+def test_all_served_and_results_routed():
+    lib = FakeLib()
+    ev = _stream([(0.0, 8, [0.001, 0.002, 0.06]), (0.01, 16, [0.02]), (0.03, 8, [0.031, 0.032])])
+    srv = serving.Server(1 << 40, slots=4, lib=lib, new_stream=FakeStream, keep_results=True)
+    recs, wall = srv.run(ev)
+    assert all(r.ok for r in recs.values())
+    for _, r in ev:
+        if isinstance(r, serving.SolveRequest):
+            np.testing.assert_array_equal(srv.results[r.rid], 2.0 * r.rhs)
+    assert sorted(lib.freed) == [0, 4, 6]
+    assert srv.reserved == 0 and not srv.handles
+
+
+def test_continuous_admission_overlaps():
+    # system 1 arrives while system 0 factors: it starts before 0 finishes
+    lib = FakeLib(tf=0.3)
+    ev = _stream([(0.0, 8, [0.35]), (0.02, 8, [0.36])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    recs, _ = srv.run(ev)
+    assert recs[2].start < recs[0].done
+    assert lib.max_live == 2 and srv.peak_active == 2
+
+
+def test_solves_coalesced_while_factoring():
+    lib = FakeLib(tf=0.2)
+    ev = _stream([(0.0, 8, [0.01 + 0.01 * i for i in range(10)])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream, max_batch=64)
+    recs, _ = srv.run(ev)
+    assert lib.solve_calls[0] == (0, 10)
+    assert all(r.batch == 10 for r in recs.values() if r.kind == "solve")
+
+
+def test_max_batch_splits():
+    lib = FakeLib(tf=0.2)
+    ev = _stream([(0.0, 8, [0.01 + 0.001 * i for i in range(10)])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream, max_batch=4)
+    srv.run(ev)
+    assert [c[1] for c in lib.solve_calls] == [4, 4, 2]
+
+
+def test_budget_bounds_reservation():
+    lib = FakeLib(tf=0.05)
+    reqs = [_system(0, 0, 16, 0)]
+    one = serving.peak_bytes(reqs[0], acr.ACR_FP32TC_IR)
+    ev = _stream([(0.001 * i, 16, []) for i in range(6)])
+    budget = 2 * one + one // 2   # room for two factorizations in flight
+    srv = serving.Server(budget, slots=6, lib=lib, new_stream=FakeStream)
+    recs, _ = srv.run(ev)
+    assert all(r.ok for r in recs.values())
+    assert srv.peak_reserved <= budget
+    assert lib.max_live <= 2
+
+
+def test_oversized_request_still_admitted_alone():
+    lib = FakeLib(tf=0.02)
+    ev = _stream([(0.0, 16, [0.001])])
+    srv = serving.Server(1, slots=2, lib=lib, new_stream=FakeStream)
+    recs, _ = srv.run(ev)
+    assert all(r.ok for r in recs.values())
+
+
+def test_failed_factor_fails_its_solves_only():
+    lib = FakeLib(tf=0.05, fail={12})
+    ev = _stream([(0.0, 12, [0.001, 0.2]), (0.0, 8, [0.01])])
+    srv = serving.Server(1 << 40, slots=4, lib=lib, new_stream=FakeStream)
+    recs, _ = srv.run(ev)
+    assert [recs[i].ok for i in range(3)] == [False, False, False]
+    assert recs[3].ok and recs[4].ok
+    assert len(srv.errors) == 1 and "planted" in srv.errors[0][1]
+
+
+def test_summary():
+    lib = FakeLib(tf=0.01, ts=0.005)
+    ev = _stream([(0.0, 8, [0.001 * i for i in range(1, 6)])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    recs, wall = srv.run(ev)
+    s = serving.summarize(recs, wall)
+    assert s["solve"]["count"] == 5 and s["factor"]["count"] == 1
+    assert s["solve"]["p50_ms"] <= s["solve"]["p99_ms"]
+    assert s["failed"] == 0 and s["solves_per_s"] > 0
+
+
+def test_request_stream_seeded():
+    e1 = serving.make_requests(30, rate=100.0, seed=3, sizes=(8, 16), probs=(0.5, 0.5), max_solves=5)
+    e2 = serving.make_requests(30, rate=100.0, seed=3, sizes=(8, 16), probs=(0.5, 0.5), max_solves=5)
+    assert len(e1) == 30 and [t for t, _ in e1] == [t for t, _ in e2]
+    times = [t for t, _ in e1]
+    assert times == sorted(times)
+    nsys = [r for _, r in e1 if isinstance(r, serving.SystemRequest)]
+    for s in nsys:
+        solves = [r for _, r in e1 if isinstance(r, serving.SolveRequest) and r.sys_rid == s.rid]
+        assert len(solves) == s.nsolve >= 1
+        assert s.leaf == 32 and s.tol == 1e-6
