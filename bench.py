@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-8, help="HODLR compression tolerance (0: dense blocks)")
     p.add_argument("--leaf", type=int, default=64, help="HODLR leaf size")
     p.add_argument("--no-dense", action="store_true", help="skip the dense-block (tol 0) comparison")
+    p.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving mix (0: skip)")
+    p.add_argument("--serving-rate", type=float, default=200.0, help="offered rate of the serving mix, req/s")
     return p.parse_args()
 
 
@@ -61,6 +63,35 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_max(x: float, ws: int, device=None) -> float:
+    """The maximum of `x` over the ranks (the job's time is its slowest
+    replica's); `x` itself on one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, ws: int, elapsed_max: float) -> float:
+    """Whole-job throughput of `ws` independent replicas: every rank
+    processes `units_per_rank` units; the job ends with its slowest rank."""
+    return units_per_rank * ws / elapsed_max
+
+
+def bench_config(args, P, prec, ws=1):
+    """The `config` object of the JSON line (shared by both arms)."""
+    return {"workload": f"helmholtz{args.n}: 2D Helmholtz -Lap u - kappa^2 u, {args.n}x{args.n} grid, "
+                        f"N={P.N}, {P.nblk} blocks of {P.b}x{P.b}, {args.nrhs} RHS, 16 points per wavelength "
+                        "+-20% seeded kappa, refinement to 1e-8",
+            "nblk": P.nblk, "blksz": P.b, "nrhs": args.nrhs, "precision": prec,
+            "hodlr_tol": args.tol, "hodlr_leaf": args.leaf,
+            "l2": "inputs larger than L2 (banded operator and level arrays, GBs, vs 129 MB L2)",
+            "parallelism": f"replicas x{ws}"}
 
 
 def workload(n, nrhs):
@@ -212,7 +243,7 @@ def cpu_baseline(P, nrhs, nblocks):
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
-        return
+        return  # the oracle arm runs on rank 0 only
     P, _ = workload(args.n, args.nrhs)
     nb = min(16, P.nblk)
     times = []
@@ -227,7 +258,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"helmholtz{args.n}", "nblk": P.nblk, "blksz": P.b, "nrhs": args.nrhs},
+            "config": bench_config(args, P, args.prec if args.prec != "auto" else "fp32tc", ws),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -310,11 +341,8 @@ def run_ours(args):
     # the library's calls are host-synchronous: device time between the events
     # includes the host gaps between launches, so take the larger of the two
     elapsed = max(dev_ms / 1e3, wall)
-    if ws > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = nrhs * args.steps * ws / elapsed
+    elapsed = reduce_max(elapsed, ws, dev)
+    value = replica_value(nrhs * args.steps, ws, elapsed)
 
     last = stats[-1]
     kernel = "gemm_tc" if prec == "fp32tc" else ("gemm_simt_f32" if prec == "fp32" else "gemm_simt_f64")
@@ -347,13 +375,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32tc": "f32(tf32x3 tc)+f64", "fp32": "f32+f64", "fp64": "f64"}[prec],
             "data": "synthetic",
-            "config": {"workload": f"helmholtz{args.n}: 2D Helmholtz -Lap u - kappa^2 u, {args.n}x{args.n} grid, "
-                                   f"N={N}, {P.nblk} blocks of {P.b}x{P.b}, {nrhs} RHS, 16 points per wavelength "
-                                   "+-20% seeded kappa, refinement to 1e-8",
-                       "nblk": P.nblk, "blksz": P.b, "nrhs": nrhs, "precision": prec,
-                       "hodlr_tol": args.tol, "hodlr_leaf": args.leaf,
-                       "l2": "inputs larger than L2 (factor storage %.1f GB vs 129 MB L2)" % (last["factor_bytes"] / 1e9),
-                       "parallelism": f"replicas x{ws}"},
+            "config": bench_config(args, P, prec, ws),
             "factor_s": statistics.median(s["factor_ms"] for s in stats) / 1e3,
             "solve_s": statistics.median(s["solve_ms"] for s in stats) / 1e3,
             "solves_per_s_resident": nrhs / (statistics.median(s["solve_ms"] for s in stats) / 1e3),
@@ -420,6 +442,17 @@ def run_ours(args):
         line["e2e"] = {"value": nrhs * ws / et, "unit": UNIT,
                        "h2d_bytes_per_step": int(a.nbytes + D3.nbytes + c.nbytes + F.nbytes),
                        "d2h_bytes_per_step": int(F.nbytes), "s_per_step": et}
+
+    # ---- the serving mix (rank 0's replica) ---------------------------------
+    if rank == 0 and args.serving_requests > 0:
+        from paper_1604_00617_gb300 import serving
+        sv = serving.serve(nreq=args.serving_requests, rate=args.serving_rate, seed=42,
+                           budget_gb=150.0, slots=4)
+        sv["workload"] = ("Poisson stream of requests: variable-coefficient diffusion or convection-diffusion "
+                          "systems (50/50, seeded per system) at n in {128,256,512,1024} with p {.4,.3,.2,.1}, "
+                          "HODLR tol 1e-6 (leaf 32 up to n=256, 64 above), each followed by 1-64 single-RHS "
+                          "solves, FP32-TC factor + FP64 FGMRES to 1e-8, 150 GB admission budget, 4 slots")
+        line["serving"] = sv
 
     if rank == 0 and not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline(P, nrhs, min(args.cpu_blocks, P.nblk))
