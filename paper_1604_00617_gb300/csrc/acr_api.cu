@@ -284,37 +284,41 @@ int compress_factor(acr_ctx* h) {
     const int npb = (1 << (L + 1)) - 2;  // off-diagonal nodes per block
 
     // ---- sketch, QR + SVD, V for every tree level ------------------------------
+    // Two passes per tree level: every node is sketched with k1 = 16 columns
+    // (ranks at most k1 - 4 are resolved by it); only the nodes whose sketch
+    // saturates are sketched again with k = kmax.  Most nodes of the low
+    // reduction levels have ranks of a few units, so the QR + SVD work, which
+    // grows with k^2, is paid at k = kmax only where it is needed.
     const int omr = std::max(1, b / 2);
     DevBuf om;
     CK(om.alloc((size_t)omr * kmax * sizeof(T), s));
     CK(hodlr_omega<T>(om.as<T>(), (long long)omr * kmax, 0x5eedacc0ull + (uint64_t)b, s));
-    std::vector<DevBuf> Uk(L + 1), Vk(L + 1), Sg(L + 1);
-    std::vector<int> kl(L + 1, 0);
-    std::vector<std::vector<T>> hsig(L + 1);
-    for (int l = 1; l <= L; ++l) {
-        const int sz = b >> l, nn = NB << l;
-        int k = std::min(kmax, sz);
-        k -= k & 1;
-        if (k < 2) k = 2;
+    std::vector<DevBuf> Uk(L + 1), Vk(L + 1), Uk2(L + 1), Vk2(L + 1);
+    std::vector<int> kl(L + 1, 0), kl2(L + 1, 0);
+    std::vector<std::vector<T>> hsig(L + 1), hsig2(L + 1);
+    std::vector<std::vector<int>> sat(L + 1);       // node ids (g << l | ni) of the second pass
+    std::vector<std::vector<int>> sat_pos(L + 1);   // id -> position in sat, or -1
+    // one pass over the nodes `ids` of tree level l with k sketch columns
+    auto sketch = [&](int l, const std::vector<int>& ids, int k, DevBuf& U, DevBuf& V, std::vector<T>& sig) -> int {
+        const int sz = b >> l, nn = (int)ids.size();
+        if (nn == 0) return ACR_OK;
         if (node_svd_kz<T>(sz, k) == 0) return fail(ACR_ERR_INVALID_ARG, "HODLR node %d too large", sz);
-        kl[l] = k;
         std::vector<const T*> pa(nn), pb(nn);
         std::vector<T*> pc(nn);
-        DevBuf Y;
+        DevBuf Y, Sg;
         CK(Y.alloc((size_t)nn * sz * k * sizeof(T), s));
-        CK(Uk[l].alloc((size_t)nn * sz * k * sizeof(T), s));
-        CK(Vk[l].alloc((size_t)nn * sz * k * sizeof(T), s));
-        CK(Sg[l].alloc((size_t)nn * k * sizeof(T), s));
-        for (int g = 0; g < NB; ++g)
-            for (int ni = 0; ni < (1 << l); ++ni) {
-                const int p = ni >> 1, lower = ni & 1;
-                const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
-                const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
-                const size_t id = ((size_t)g << l) + ni;
-                pa[id] = blocks[g] + r0 + (size_t)c0 * b;
-                pb[id] = om.as<T>();
-                pc[id] = Y.as<T>() + id * sz * k;
-            }
+        CK(U.alloc((size_t)nn * sz * k * sizeof(T), s));
+        CK(V.alloc((size_t)nn * sz * k * sizeof(T), s));
+        CK(Sg.alloc((size_t)nn * k * sizeof(T), s));
+        for (int i = 0; i < nn; ++i) {
+            const int g = ids[i] >> l, ni = ids[i] & ((1 << l) - 1);
+            const int p = ni >> 1, lower = ni & 1;
+            const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
+            const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
+            pa[i] = blocks[g] + r0 + (size_t)c0 * b;
+            pb[i] = om.as<T>();
+            pc[i] = Y.as<T>() + (size_t)i * sz * k;
+        }
         DevBuf dpa, dpb, dpc;
         CK(dpa.alloc(nn * sizeof(void*), s));
         CK(dpb.alloc(nn * sizeof(void*), s));
@@ -323,19 +327,52 @@ int compress_factor(acr_ctx* h) {
         CK(cudaMemcpyAsync(dpb.p, pb.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dpc.p, pc.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
         CK(gemm_gen<T>(dpa.as<const T*>(), dpb.as<const T*>(), dpc.as<T*>(), nn, sz, k, sz, b, omr, sz, false, s));
-        CK(node_svd<T>(Y.as<T>(), Uk[l].as<T>(), Sg[l].as<T>(), nn, sz, k, s));
+        CK(node_svd<T>(Y.as<T>(), U.as<T>(), Sg.as<T>(), nn, sz, k, s));
         // V_k = B^T U_k
         for (int i = 0; i < nn; ++i) {
-            pb[i] = Uk[l].as<T>() + (size_t)i * sz * k;
-            pc[i] = Vk[l].as<T>() + (size_t)i * sz * k;
+            pb[i] = U.as<T>() + (size_t)i * sz * k;
+            pc[i] = V.as<T>() + (size_t)i * sz * k;
         }
         CK(cudaStreamSynchronize(s));  // host pointer tables reused below
         CK(cudaMemcpyAsync(dpb.p, pb.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dpc.p, pc.data(), nn * sizeof(void*), cudaMemcpyHostToDevice, s));
         CK(gemm_gen<T>(dpa.as<const T*>(), dpb.as<const T*>(), dpc.as<T*>(), nn, sz, k, sz, b, sz, sz, true, s));
-        hsig[l].resize((size_t)nn * k);
-        CK(cudaMemcpyAsync(hsig[l].data(), Sg[l].p, (size_t)nn * k * sizeof(T), cudaMemcpyDeviceToHost, s));
+        sig.resize((size_t)nn * k);
+        CK(cudaMemcpyAsync(sig.data(), Sg.p, (size_t)nn * k * sizeof(T), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        return ACR_OK;
+    };
+    auto rank_of = [&](const T* sg, int k) {
+        int r = 0;
+        if (sg[0] > T(0))
+            while (r < k && (double)sg[r] > tol * (double)sg[0]) ++r;
+        return r;
+    };
+    for (int l = 1; l <= L; ++l) {
+        const int sz = b >> l, nn = NB << l;
+        int kbig = std::min(kmax, sz);
+        kbig -= kbig & 1;
+        if (kbig < 2) kbig = 2;
+        const int k1 = std::min(kbig, 16);
+        kl[l] = k1;
+        kl2[l] = kbig;
+        std::vector<int> all(nn);
+        for (int i = 0; i < nn; ++i) all[i] = i;
+        int st = sketch(l, all, k1, Uk[l], Vk[l], hsig[l]);
+        if (st) return st;
+        sat_pos[l].assign(nn, -1);
+        if (k1 < kbig) {
+            for (int i = 0; i < nn; ++i) {
+                int r = rank_of(hsig[l].data() + (size_t)i * k1, k1);
+                if (max_rank > 0 && r > max_rank) r = max_rank;
+                if (r > k1 - 4 && 2 * r < sz) {
+                    sat_pos[l][i] = (int)sat[l].size();
+                    sat[l].push_back(i);
+                }
+            }
+            st = sketch(l, sat[l], kbig, Uk2[l], Vk2[l], hsig2[l]);
+            if (st) return st;
+        }
     }
 
     // ---- ranks, layout ------------------------------------------------------------
@@ -356,14 +393,14 @@ int compress_factor(acr_ctx* h) {
             for (int id : h->bid[t][arr])
                 if (id >= 0) blk_level[id] = t;
     for (int l = 1; l <= L; ++l) {
-        const int sz = b >> l, k = kl[l];
+        const int sz = b >> l;
         for (int g = 0; g < NB; ++g)
             for (int ni = 0; ni < (1 << l); ++ni) {
                 const size_t id = ((size_t)g << l) + ni;
-                const T* sg = hsig[l].data() + id * k;
-                int r = 0;
-                if (sg[0] > T(0))
-                    while (r < k && (double)sg[r] > tol * (double)sg[0]) ++r;
+                const int sp = sat_pos[l][id];
+                const int k = sp >= 0 ? kl2[l] : kl[l];
+                const T* sg = sp >= 0 ? hsig2[l].data() + (size_t)sp * k : hsig[l].data() + id * k;
+                int r = rank_of(sg, k);
                 if (max_rank > 0 && r > max_rank) r = max_rank;
                 const bool sketch_full = (k < sz) && (r > k - 4);
                 const bool dense = sketch_full || (2 * r >= sz);
@@ -403,25 +440,38 @@ int compress_factor(acr_ctx* h) {
         CK(cudaMemcpyAsync(dlo.p, lo.data(), (size_t)NB * sizeof(long long), cudaMemcpyHostToDevice, s));
         CK(pack_leaves<T>(dblk.as<const T*>(), dlo.as<long long>(), NB, b, leaf, h->hpool.as<T>(), s));
         for (int l = 1; l <= L; ++l) {
-            const int sz = b >> l, nn = NB << l;
-            std::vector<HNode> lv(nn);
-            std::vector<const T*> src(nn);
+            const int sz = b >> l, nn = NB << l, ns = (int)sat[l].size();
+            // first launch: every node, the second-pass ones marked to skip
+            // (rank -2); second launch: the second-pass nodes
+            std::vector<HNode> lv((size_t)nn + ns);
+            std::vector<const T*> src((size_t)nn + ns);
             for (int g = 0; g < NB; ++g)
                 for (int ni = 0; ni < (1 << l); ++ni) {
                     const size_t id = ((size_t)g << l) + ni;
-                    lv[id] = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
+                    const HNode hn = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
                     const int p = ni >> 1, lower = ni & 1;
                     const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
                     const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
-                    src[id] = blocks[g] + r0 + (size_t)c0 * b;
+                    const T* B = blocks[g] + r0 + (size_t)c0 * b;
+                    const int sp = sat_pos[l][id];
+                    lv[id] = hn;
+                    src[id] = B;
+                    if (sp >= 0) {
+                        lv[id].rank = -2;
+                        lv[(size_t)nn + sp] = hn;
+                        src[(size_t)nn + sp] = B;
+                    }
                 }
             DevBuf dm, ds;
-            CK(dm.alloc((size_t)nn * sizeof(HNode), s));
-            CK(ds.alloc((size_t)nn * sizeof(void*), s));
-            CK(cudaMemcpyAsync(dm.p, lv.data(), (size_t)nn * sizeof(HNode), cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(ds.p, src.data(), (size_t)nn * sizeof(void*), cudaMemcpyHostToDevice, s));
+            CK(dm.alloc(lv.size() * sizeof(HNode), s));
+            CK(ds.alloc(src.size() * sizeof(void*), s));
+            CK(cudaMemcpyAsync(dm.p, lv.data(), lv.size() * sizeof(HNode), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(ds.p, src.data(), src.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
             CK(pack_nodes<T>(dm.as<HNode>(), 0, nn, Uk[l].as<T>(), Vk[l].as<T>(), ds.as<const T*>(), sz, kl[l], b,
                              h->hpool.as<T>(), s));
+            if (ns > 0)
+                CK(pack_nodes<T>(dm.as<HNode>(), nn, ns, Uk2[l].as<T>(), Vk2[l].as<T>(), ds.as<const T*>() + nn, sz,
+                                 kl2[l], b, h->hpool.as<T>(), s));
             CK(cudaStreamSynchronize(s));  // host tables of this level
         }
         CK(cudaStreamSynchronize(s));
@@ -715,7 +765,11 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         CK(mark(0));
         if (b0 && t == 0)
             CK(tridiag_inverse<T>(dD, n, b, h->P<T>(L.off_dinv), dinfo.as<int>() + info_off[t], s));
-        else
+        else if (tc && gj_tc_supported(b)) {
+            if constexpr (sizeof(T) == 4)
+                CK(gj_inverse_tc(h->P<T>(L.off_dinv), b, L.ne, dinfo.as<int>() + info_off[t], dpiv.as<int>(),
+                                 dterr.as<int>(), s));
+        } else
             CK(gj_inverse<T>(h->P<T>(L.off_dinv), b, L.ne, dinfo.as<int>() + info_off[t], dpiv.as<int>(), s));
         CK(mark(0));
         inv_l += launch_count() - c0;

@@ -113,8 +113,22 @@ size_t tc_map_bytes();
 // Encode the tensor map of `count` contiguous b x b column-major FP32 blocks
 // starting at base, as left (role 0) or right (role 1) operand.  0 on success.
 int tc_encode_map(void* map_out, const float* base, int b, int count, int role);
+// Same for `count` matrices of d0 (contiguous) x d1 elements.
+int tc_encode_map_dims(void* map_out, const float* base, int d0, int d1, int count, int role);
 // d_err: set to 1 if a CTA gave up on a bounded wait (then later CTAs skip).
 cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s);
+// General form: out[:, cols] (b rows, ld b) = alpha * A_t[:, ka0 : ka0 + kdim] B_t[0 : kdim, cols] + beta * cin,
+// tiles_n column tiles of 128, tile tn at column tile (tn < nskip ? tn : tn + nshift).
+// b and kdim multiples of 128 and 32; A's k coordinate offset ka0 a multiple of 32.
+// lolo != 0 adds the fourth split term Alo Blo.
+cudaError_t gemm_tc_ex(const TcProb* d_probs, int nprob, const void* d_maps, int b, int kdim, int ka0,
+                       int tiles_n, int nskip, int nshift, int lolo, int* d_err, cudaStream_t s);
+
+// Batched FP32 inversion whose rank-128 outer-panel updates run on the tensor
+// cores (gemm_tc_ex); b a multiple of 128, b >= 256.  Same pivoting and
+// results (to FP32 rounding) as gj_inverse<float>.
+bool gj_tc_supported(int b);
+cudaError_t gj_inverse_tc(float* mats, int b, int count, int* info, int* ws_piv, int* d_err, cudaStream_t s);
 
 // --- HODLR blocks (k_hodlr.cu) ------------------------------------------------
 // Node of a compressed block: rank >= 0: U (s x rank) then V (s x rank) at off

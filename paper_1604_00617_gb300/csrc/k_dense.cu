@@ -16,8 +16,10 @@
 #include <cfloat>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "acr_internal.h"
 
@@ -497,25 +499,101 @@ k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, int colA, int colB,
         sl[i] = slot[rbase + i];
         plain &= sl[i] < 0;
     }
+    if (plain) {
+        // loads of a group of columns before its stores (the stores could
+        // alias later loads, so interleaving them serialises the round trips)
+        constexpr int JG = TN < 8 ? TN : 8;
+#pragma unroll
+        for (int jg = 0; jg < TN; jg += JG) {
+            VT v[JG];
+#pragma unroll
+            for (int jj = 0; jj < JG; ++jj) {
+                const int jc = j0 + tx + (jg + jj) * RX;
+                const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
+                if (jc < nJ) v[jj] = *reinterpret_cast<const VT*>(G + rbase + (size_t)c * b);
+            }
+#pragma unroll
+            for (int jj = 0; jj < JG; ++jj) {
+                const int jc = j0 + tx + (jg + jj) * RX;
+                if (jc >= nJ) continue;
+                const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
+                T* pv = reinterpret_cast<T*>(&v[jj]);
+#pragma unroll
+                for (int i = 0; i < V; ++i) pv[i] += acc[i][jg + jj];
+                *reinterpret_cast<VT*>(G + rbase + (size_t)c * b) = v[jj];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
         const int jc = j0 + tx + j * RX;
         if (jc >= nJ) continue;
         const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
         T* gp = G + rbase + (size_t)c * b;
-        if (plain) {
-            VT v = *reinterpret_cast<const VT*>(gp);
-            T* pv = reinterpret_cast<T*>(&v);
-#pragma unroll
-            for (int i = 0; i < V; ++i) pv[i] += acc[i][j];
-            *reinterpret_cast<VT*>(gp) = v;
-        } else {
+        {
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const T base = (sl[i] < 0) ? gp[i] : (sl[i] < kb ? T(0) : st[(size_t)sl[i] * b + c]);
                 gp[i] = base + acc[i][j];
             }
         }
+    }
+}
+
+// Gather of the tensor-core form of the rank-kb update of panel [k0, k0+kb):
+// the pivot rows' values at every column go, transposed (k fastest), to stT
+// (b x kb per matrix: the K-major right operand), and the rows the update
+// treats specially get their base value in place at every column outside the
+// panel: 0 at the pivot positions, and at a row that received an interchanged
+// row, that row's values.  The product G[:, c] += G[:, panel] stT[c, :]^T
+// then completes the same update as k_gj_update_* (for columns outside the
+// panel).  Each CTA owns 32 columns: it reads all its values before writing.
+template <class T>
+__global__ void k_gj_gather_tc(T* __restrict__ mats, int b, int k0, int kb, const int* __restrict__ pivs,
+                               T* __restrict__ stT) {
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    int* perm = reinterpret_cast<int*>(sh_raw);  // b
+    int* slot = perm + b;                        // b
+    int* list = slot + b;                        // kb
+    T* vals = reinterpret_cast<T*>(sh_raw + (((size_t)(2 * b + kb) * sizeof(int) + 15) & ~(size_t)15));  // 2kb x 32
+    __shared__ int s_cnt;
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* piv = pivs + (size_t)blockIdx.y * b;
+    T* st = stT + (size_t)blockIdx.y * b * kb;
+    for (int r = threadIdx.x; r < b; r += blockDim.x) { perm[r] = r; slot[r] = -1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int kk = 0; kk < kb; ++kk) {
+            const int k = k0 + kk, p = piv[k];
+            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+            slot[k] = kk;
+        }
+        int cnt = 0;
+        for (int kk = 0; kk < kb; ++kk) {
+            const int p = piv[k0 + kk];
+            if (p >= k0 + kb && slot[p] < 0) { slot[p] = kb + cnt; list[cnt++] = p; }
+        }
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    const int ns = kb + s_cnt;
+    const int c0 = blockIdx.x * 32;
+    for (int i = threadIdx.x; i < ns * 32; i += blockDim.x) {
+        const int sl = i >> 5, j = i & 31, c = c0 + j;
+        const int r = sl < kb ? k0 + sl : list[sl - kb];
+        vals[i] = c < b ? G[perm[r] + (size_t)c * b] : T(0);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb * 32; i += blockDim.x) {
+        const int sl = i % kb, j = i / kb, c = c0 + j;
+        if (c < b) st[(size_t)c * kb + sl] = vals[sl * 32 + j];
+    }
+    for (int i = threadIdx.x; i < ns * 32; i += blockDim.x) {
+        const int sl = i >> 5, j = i & 31, c = c0 + j;
+        if (c >= b || (c >= k0 && c < k0 + kb)) continue;
+        const int r = sl < kb ? k0 + sl : list[sl - kb];
+        G[r + (size_t)c * b] = sl < kb ? T(0) : vals[i];
     }
 }
 
@@ -583,11 +661,20 @@ static int gj_outer_width(int b) {
 // is done, one rank-KO update (the same identity with panel width KO) brings
 // every other column up to date.  Each column outside the outer panel is read
 // and written once per outer panel instead of once per inner panel.
+// Tensor-core outer update: the transposed pivot-row buffer, its problems
+// (one per matrix) and tensor maps (0: the matrices, 1: the buffer).
+struct GjTc {
+    float* stT;
+    const TcProb* probs;
+    const void* maps;
+    int* err;
+};
+
 template <class T>
 static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv, T* amax, T* stash, int* slotmap,
-                              cudaStream_t s) {
+                              cudaStream_t s, const GjTc* tco = nullptr) {
     constexpr int KB = sizeof(T) == 8 ? 16 : 32;
-    const int KO = gj_outer_width<T>(b);
+    const int KO = tco ? 128 : gj_outer_width<T>(b);
     cudaMemsetAsync(amax, 0, sizeof(T) * count, s);
     k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
     count_launches(1);
@@ -627,7 +714,22 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
             count_launches(1);
             update(k0, kbi, K0, K0 + KOi);  // inside the outer panel
         }
-        update(K0, KOi, 0, b);  // everything else, once per outer panel
+        // everything else, once per outer panel
+        if constexpr (sizeof(T) == 4) {
+            if (tco) {
+                const size_t gsm = (((size_t)(2 * b + KOi) * sizeof(int) + 15) & ~(size_t)15) +
+                                   (size_t)2 * KOi * 32 * sizeof(T);
+                ensure_smem((const void*)k_gj_gather_tc<T>, gsm);
+                k_gj_gather_tc<T><<<dim3((b + 31) / 32, count), 256, gsm, s>>>(mats, b, K0, KOi, ws_piv, tco->stT);
+                count_launches(1);
+                const int nt = b / 128 - KOi / 128;
+                cudaError_t e =
+                    gemm_tc_ex(tco->probs, count, tco->maps, b, KOi, K0, nt, K0 / 128, KOi / 128, 0, tco->err, s);
+                if (e != cudaSuccess) return e;
+                continue;
+            }
+        }
+        update(K0, KOi, 0, b);
     }
     dim3 gu((b + 255) / 256, count);
     k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);
@@ -665,10 +767,60 @@ cudaError_t gj_inverse(T* mats, int b, int count, int* info, int* ws_piv, cudaSt
     return e;
 }
 
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool gj_tc_supported(int b) { return tc_supported(b) && b >= 256 && gj_small_smem<float>(b) > 200 * 1024; }
+
+cudaError_t gj_inverse_tc(float* mats, int b, int count, int* info, int* ws_piv, int* d_err, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (!gj_tc_supported(b)) return cudaErrorInvalidValue;
+    constexpr int KB = 32, KO = 128;
+    cudaMemsetAsync(info, 0, sizeof(int) * count, s);
+    const size_t mb = tc_map_bytes();
+    // one allocation: amax | inner stash (2 KB rows) | slot map | stT | problems | maps
+    const size_t o_stash = al256(sizeof(float) * count);
+    const size_t o_slot = o_stash + al256(sizeof(float) * (size_t)count * 2 * KB * b);
+    const size_t o_stT = o_slot + al256(sizeof(int) * (size_t)count * b);
+    const size_t o_prob = o_stT + al256(sizeof(float) * (size_t)count * KO * b);
+    const size_t o_maps = o_prob + al256(sizeof(TcProb) * count);
+    const size_t total = o_maps + 2 * mb;
+    unsigned char* w = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&w), total, s);
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned char> host(total - o_prob);
+    TcProb* hp = reinterpret_cast<TcProb*>(host.data());
+    for (int z = 0; z < count; ++z) {
+        TcProb q;
+        std::memset(&q, 0, sizeof(q));
+        q.out = mats + (size_t)z * b * b;
+        q.cin = q.out;
+        q.alpha = 1.f;
+        q.beta = 1.f;
+        q.nterm = 1;
+        q.amap[0] = 0; q.az[0] = z;
+        q.bmap[0] = 1; q.bz[0] = z;
+        hp[z] = q;
+    }
+    unsigned char* hm = host.data() + (o_maps - o_prob);
+    float* stT = reinterpret_cast<float*>(w + o_stT);
+    if (tc_encode_map_dims(hm, mats, b, b, count, 0) != 0 || tc_encode_map_dims(hm + mb, stT, KO, b, count, 1) != 0) {
+        cudaFreeAsync(w, s);
+        return cudaErrorInvalidValue;
+    }
+    // pageable source: the copy is staged before the call returns
+    e = cudaMemcpyAsync(w + o_prob, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        GjTc tco{stT, reinterpret_cast<const TcProb*>(w + o_prob), w + o_maps, d_err};
+        e = gj_blocked<float>(mats, b, count, info, ws_piv, reinterpret_cast<float*>(w),
+                              reinterpret_cast<float*>(w + o_stash), reinterpret_cast<int*>(w + o_slot), s, &tco);
+    }
+    cudaFreeAsync(w, s);
+    return e;
+}
+
 // Scratch layout of gj_inverse_scratch (each part 256-byte aligned):
 // pivots (count*b ints), max|entry| (count T), row stash (count*2*kb*b T),
 // slot map (count*b ints).  The shared-memory path needs none.
-static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <class T>
 size_t gj_scratch_bytes(int b, int count) {
@@ -764,18 +916,21 @@ k_gemm_simt(const GemmProb<T>* __restrict__ probs, int b, int tiles_m) {
             __syncthreads();
         }
     }
+    // per column: the TM loads before the TM stores (out may alias cin)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
         const int c = col0 + tx + j * RX;
         if (c >= b) continue;
+        T cv[TM];
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int r = row0 + ty + i * RY;
-            if (r >= b) continue;
-            const size_t o = r + (size_t)c * b;
-            T v = P.alpha * acc[i][j];
-            if (P.cin) v += P.beta * P.cin[o];
-            P.out[o] = v;
+            cv[i] = (P.cin && r < b) ? P.cin[r + (size_t)c * b] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int r = row0 + ty + i * RY;
+            if (r < b) P.out[r + (size_t)c * b] = P.alpha * acc[i][j] + P.beta * cv[i];
         }
     }
 }
@@ -898,7 +1053,7 @@ k_sweep(const SweepProb<T>* __restrict__ probs, int b, int nrhs, int row_tiles) 
 // The multi-vector operand of each term is staged whole (b x NR) in dynamic
 // shared memory, so the column loop runs without barriers.
 template <class T, int V, int NR, int RG, int KG>
-__global__ void __launch_bounds__(RG * KG)
+__global__ void __launch_bounds__(RG * KG, (sizeof(T) == 4 && NR == 8) ? 3 : 1)
 k_sweep_vec(const SweepProb<T>* __restrict__ probs, int b, int nrhs, T* __restrict__ part) {
     using VT = typename VecT<T, V>::type;
     constexpr int NT = RG * KG, RT = RG * V;

@@ -234,6 +234,78 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
     }
     const T negl = red[0] * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
     __syncthreads();
+    // One warp runs the sweeps with R in registers: lane c holds column c.
+    // Round rnd of the round-robin schedule pairs column k-1 with rnd and
+    // rnd+q with rnd-q (mod k-1), q = 1 .. k/2-1; a lane exchanges its column
+    // with its partner by shuffles, and both lanes of a pair compute the same
+    // norms, inner product and rotation, so no barrier is needed.
+    if (k <= 32) {
+    if (warp == 0) {
+        constexpr unsigned FULL = 0xffffffffu;
+        T col[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) col[r] = (lane < k && r < k) ? R[r + lane * k] : T(0);
+        T nrm = T(0);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) nrm = fma(col[r], col[r], nrm);
+        const int km1 = k - 1;
+        for (int sweep = 0; sweep < 12; ++sweep) {
+            bool rot = false;
+            for (int rnd = 0; rnd < km1; ++rnd) {
+                int partner = lane;
+                bool is_a = false;
+                if (lane < k) {
+                    if (lane == km1) {
+                        partner = rnd;
+                        is_a = true;
+                    } else if (lane == rnd) {
+                        partner = km1;
+                    } else {
+                        partner = ((2 * rnd - lane) % km1 + km1) % km1;
+                        const int d = ((lane - rnd) % km1 + km1) % km1;
+                        is_a = d >= 1 && d <= k / 2 - 1;
+                    }
+                }
+                T pc[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) pc[r] = __shfl_sync(FULL, col[r], partner);
+                const T pn = __shfl_sync(FULL, nrm, partner);
+                T ga = T(0);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) ga = fma(col[r], pc[r], ga);
+                const T al = is_a ? nrm : pn, be = is_a ? pn : nrm;
+                if (partner != lane && al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                    const T zeta = (be - al) / (T(2) * ga);
+                    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+                    T n2 = T(0);
+                    if (is_a) {
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            col[r] = c * col[r] - sn * pc[r];
+                            n2 = fma(col[r], col[r], n2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            col[r] = sn * pc[r] + c * col[r];
+                            n2 = fma(col[r], col[r], n2);
+                        }
+                    }
+                    nrm = n2;
+                    rot = true;
+                }
+            }
+            if (!__any_sync(FULL, rot)) break;
+        }
+        if (lane < k)
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (r < k) R[r + lane * k] = col[r];
+    }
+    __syncthreads();
+    } else {
+    // wider sketches: the pairs of a round spread over the warps
     for (int sweep = 0; sweep < 12; ++sweep) {
         if (tid == 0) s_flag = 0;
         __syncthreads();
@@ -269,6 +341,7 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
         const bool converged = !s_flag;
         __syncthreads();
         if (converged) break;
+    }
     }
     // singular values and their order (decreasing, ties by index)
     for (int c = warp; c < k; c += 8) {
@@ -363,6 +436,7 @@ __global__ void k_pack_nodes(const HNode* __restrict__ meta, int node0, const T*
                              T* __restrict__ pool) {
     const int i = blockIdx.x;
     const HNode m = meta[node0 + i];
+    if (m.rank == -2) return;  // packed by another launch
     T* dst = pool + m.off;
     if (m.rank < 0) {
         const T* B = src[i];
@@ -502,97 +576,188 @@ k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tas
     }
 }
 
-template <class T, int NR>
+// 16-byte vectors of T for the row streams of pass B
+template <class T> struct HVec;
+template <> struct HVec<float> { using type = float4; static constexpr int V = 4; };
+template <> struct HVec<double> { using type = double2; static constexpr int V = 2; };
+
+// Pass B: one CTA per (problem, row tile of RT rows).  For each compressed
+// term the tile's operator is a short list of column segments -- its leaf
+// (leaf columns), then per tree level the node whose rows hold the tile: U
+// (rank columns, input t = V^T x from pass A) or a dense node (s columns,
+// input x at the partner columns).  Lanes of warp 0 read the level nodes at
+// once, all inputs are staged in one phase, then the rows of every segment
+// are streamed with 16-byte loads (column j of the concatenation goes to
+// column group j mod KG) and the groups are summed in a fixed order.
+// Split (gridDim.z > 1, part != NULL): CTA z takes the z-th of gridDim.z
+// equal chunks of each term's concatenated columns and writes raw partial
+// sums part[((z * nprob + p) * b + row) * nrhs + q]; k_hrows_reduce adds them
+// in z order.
+template <class T, int NR, int V>
 __global__ void __launch_bounds__(256)
 k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, const HNode* __restrict__ nodes,
         const HTask* __restrict__ tasks, const T* __restrict__ tbuf, const T* __restrict__ pool, int b, int leaf,
-        int L, int nrhs, int RT) {
+        int L, int nrhs, int RT, T* __restrict__ part) {
+    using VT = typename HVec<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int KG = 256 / RT;
-    T* xs = reinterpret_cast<T*>(smem_raw);           // up to (b/2) x NR
-    T* red = xs + (size_t)std::max(b / 2, leaf) * NR;  // KG x RT x NR
+    T* xs = reinterpret_cast<T*>(smem_raw);  // [W][NR], W <= b; reused for the group sums
+    __shared__ const T* s_ptr[17];
+    __shared__ long long s_src[17];
+    __shared__ int s_ld[17], s_cs[18], s_kind[17], s_rk[17];
+    const int RG = RT / V, KG = 256 / RG;
     const HSweepProb<T>& P = probs[blockIdx.y];
     const int R0 = blockIdx.x * RT;
-    const int tid = threadIdx.x, lr = tid % RT, g = tid / RT;
-    const int row = R0 + lr;
+    const int tid = threadIdx.x, rg = tid % RG, g = tid / RG;
+    const int row = R0 + rg * V;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nz = gridDim.z, z = blockIdx.z;
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
-        T acc[NR];
+        T acc[V][NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] = T(0);
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[v][q] = T(0);
         for (int t = 0; t < 2; ++t) {
             if (!P.x[t]) continue;
             if (P.dg[t]) {
-                if (g == 0)
+                if (g == 0 && z == 0)
 #pragma unroll
-                    for (int q = 0; q < NR; ++q)
-                        if (q < nq) acc[q] += P.dg[t][row] * P.x[t][row + (size_t)(q0 + q) * P.ldx];
+                    for (int v = 0; v < V; ++v)
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+                            if (q < nq) acc[v][q] += P.dg[t][row + v] * P.x[t][row + v + (size_t)(q0 + q) * P.ldx];
                 continue;
             }
             if (P.blk[t] < 0) continue;
-            const HBlk B = blks[P.blk[t]];
-            // leaf
-            const int li = R0 / leaf, rr = row - li * leaf;
-            __syncthreads();
-            for (int i = tid; i < leaf * NR; i += 256) {
-                const int c = i % leaf, q = i / leaf;
-                xs[c * NR + q] = q < nq ? xval(P, t, li * leaf + c, q0 + q) : T(0);
+            __syncthreads();  // xs and the segment table are free
+            if (warp == 0) {
+                const HBlk B = blks[P.blk[t]];
+                const int li = R0 / leaf;
+                // lane 0: the leaf; lane l (1..L): the node of tree level l
+                int kind = -1, ld = 0, ncol = 0, rk = 0;
+                const T* ptr = nullptr;
+                long long src = 0;
+                if (lane == 0) {
+                    kind = 0;
+                    ptr = pool + B.leaf_off + (size_t)li * leaf * leaf + (R0 - li * leaf);
+                    ld = leaf;
+                    ncol = leaf;
+                    src = (long long)li * leaf;
+                } else if (lane <= L) {
+                    const int l = lane, sz = b >> l, ni = R0 / sz;
+                    const HNode hn = nodes[B.node_base + (1 << l) - 2 + ni];
+                    const int r0 = ni * sz;
+                    ld = sz;
+                    ptr = pool + hn.off + (R0 - r0);
+                    if (hn.rank < 0) {
+                        kind = 0;
+                        ncol = sz;
+                        src = (long long)(ni ^ 1) * sz;
+                    } else if (hn.rank > 0) {
+                        kind = 1;
+                        ncol = hn.rank;
+                        rk = hn.rank;
+                        src = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
+                    }
+                }
+                // exclusive prefix of the widths over lanes 0..L, in lane order
+                int cs = ncol;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, cs, o);
+                    if (lane >= o) cs += y;
+                }
+                if (lane <= L) {
+                    s_ptr[lane] = ptr;
+                    s_src[lane] = src;
+                    s_ld[lane] = ld;
+                    s_kind[lane] = kind;
+                    s_rk[lane] = rk;
+                    s_cs[lane + 1] = cs;
+                }
+                if (lane == 0) s_cs[0] = 0;
             }
             __syncthreads();
-            const T* Lm = pool + B.leaf_off + (size_t)li * leaf * leaf;
-            for (int c = g; c < leaf; c += KG) {
-                const T m = Lm[rr + (size_t)c * leaf];
-#pragma unroll
-                for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[c * NR + q], acc[q]);
+            // this CTA's columns [J0, J1) of the concatenation
+            const int Wall = s_cs[L + 1];
+            const int JS = (Wall + nz - 1) / nz;
+            const int J0 = min(Wall, z * JS), J1 = min(Wall, J0 + JS);
+            const int W = J1 - J0;
+            // stage the inputs of those columns: xs[(j - J0) * NR + q]
+            for (int i = tid; i < W * NR; i += 256) {
+                const int j = J0 + i % W, q = i / W;
+                int sg = 0;
+                while (s_cs[sg + 1] <= j) ++sg;
+                const int c = j - s_cs[sg];
+                T xv = T(0);
+                if (q < nq) {
+                    if (s_kind[sg] == 1) xv = tbuf[s_src[sg] + c + (size_t)(q0 + q) * s_rk[sg]];
+                    else xv = xval(P, t, (int)s_src[sg] + c, q0 + q);
+                }
+                xs[(j - J0) * NR + q] = xv;
             }
-            // tree levels
-            for (int l = 1; l <= L; ++l) {
-                const int s = b >> l, ni = R0 / s;
-                const HNode hn = nodes[B.node_base + (1 << l) - 2 + ni];
-                const int r0 = ni * s, c0 = (ni ^ 1) * s;
-                const T* d = pool + hn.off;
-                __syncthreads();
-                if (hn.rank < 0) {
-                    for (int i = tid; i < s * NR; i += 256) {
-                        const int c = i % s, q = i / s;
-                        xs[c * NR + q] = q < nq ? xval(P, t, c0 + c, q0 + q) : T(0);
-                    }
-                    __syncthreads();
-                    for (int c = g; c < s; c += KG) {
-                        const T m = d[(row - r0) + (size_t)c * s];
+            __syncthreads();
+            for (int sg = 0; sg <= L; ++sg) {
+                const int cs = s_cs[sg], ce = min(s_cs[sg + 1], J1);
+                const int cb = max(cs, J0);
+                if (ce <= cb) continue;
+                const T* __restrict__ mp = s_ptr[sg] + rg * V;
+                const int ld = s_ld[sg];
+                int j = cb + ((g - cb) % KG + KG) % KG;
+#pragma unroll 4
+                for (; j < ce; j += KG) {
+                    const VT mv = *reinterpret_cast<const VT*>(mp + (size_t)(j - cs) * ld);
+                    const T* mvp = reinterpret_cast<const T*>(&mv);
 #pragma unroll
-                        for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[c * NR + q], acc[q]);
-                    }
-                } else if (hn.rank > 0) {
-                    const int rk = hn.rank;
-                    const long long toff = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
-                    for (int i = tid; i < rk * NR; i += 256) {
-                        const int ii = i % rk, q = i / rk;
-                        xs[ii * NR + q] = q < nq ? tbuf[toff + ii + (size_t)(q0 + q) * rk] : T(0);
-                    }
-                    __syncthreads();
-                    for (int ii = g; ii < rk; ii += KG) {
-                        const T m = d[(row - r0) + (size_t)ii * s];
+                    for (int q = 0; q < NR; ++q) {
+                        const T xq = xs[(j - J0) * NR + q];
 #pragma unroll
-                        for (int q = 0; q < NR; ++q) acc[q] = fma(m, xs[ii * NR + q], acc[q]);
+                        for (int v = 0; v < V; ++v) acc[v][q] = fma(mvp[v], xq, acc[v][q]);
                     }
                 }
             }
         }
         __syncthreads();
+        T* red = xs;  // [KG][RT][NR]
 #pragma unroll
-        for (int q = 0; q < NR; ++q) red[((size_t)g * RT + lr) * NR + q] = acc[q];
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) red[((size_t)g * RT + rg * V + v) * NR + q] = acc[v][q];
         __syncthreads();
         for (int i = tid; i < RT * NR; i += 256) {
             const int r = i % RT, q = i / RT;
             if (q < nq) {
                 T sum = T(0);
                 for (int gg = 0; gg < KG; ++gg) sum += red[((size_t)gg * RT + r) * NR + q];
-                T o = P.alpha * sum;
-                if (P.cin) o += P.cin[R0 + r + (size_t)(q0 + q) * P.ldc];
-                P.out[R0 + r + (size_t)(q0 + q) * P.ldo] = o;
+                if (part) {
+                    part[(((size_t)z * gridDim.y + blockIdx.y) * b + R0 + r) * nrhs + q0 + q] = sum;
+                } else {
+                    T o = P.alpha * sum;
+                    if (P.cin) o += P.cin[R0 + r + (size_t)(q0 + q) * P.ldc];
+                    P.out[R0 + r + (size_t)(q0 + q) * P.ldo] = o;
+                }
             }
         }
+    }
+}
+
+// out = cin + alpha * sum_z part[z], fixed summation order.
+template <class T>
+__global__ void k_hrows_reduce(const HSweepProb<T>* __restrict__ probs, int nprob, int b, int nrhs, int nsplit,
+                               const T* __restrict__ part) {
+    const long long total = (long long)nprob * b * nrhs;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % nrhs);
+        const long long pr = t / nrhs;
+        const int row = (int)(pr % b), p = (int)(pr / b);
+        T sum = T(0);
+        for (int zz = 0; zz < nsplit; ++zz) sum += part[(((size_t)zz * nprob + p) * b + row) * nrhs + q];
+        const HSweepProb<T>& P = probs[p];
+        T o = P.alpha * sum;
+        if (P.cin) o += P.cin[row + (size_t)q * P.ldc];
+        P.out[row + (size_t)q * P.ldo] = o;
     }
 }
 
@@ -606,9 +771,24 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     // tile lies inside one leaf and inside one node of every tree level
     int RT = 1;
     while (RT < 64 && leaf % (RT * 2) == 0) RT *= 2;
-    const size_t sm = ((size_t)std::max(b / 2, leaf) * NR + (size_t)256 * NR) * sizeof(T);
+    constexpr int V = HVec<T>::V;
+    if (RT % V || leaf % V || L > 16) return cudaErrorInvalidValue;
+    // xs holds the staged inputs (<= b columns), then the KG x RT group sums
+    const size_t sm = (size_t)std::max(b, 256 * V) * NR * sizeof(T);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
-    const dim3 gb(b / RT, nprob);
+    // few row tiles: split each tile's columns over CTAs so that every SM streams
+    int nsplit = 1;
+    const long long tiles = (long long)nprob * (b / RT);
+    if (tiles < 2 * 152) {
+        nsplit = (int)((4 * 152 + tiles - 1) / tiles);
+        nsplit = std::min(nsplit, std::max(1, b / 64));
+    }
+    T* part = nullptr;
+    if (nsplit > 1 && cudaMallocAsync(&part, sizeof(T) * (size_t)nsplit * nprob * b * nrhs, s) != cudaSuccess) {
+        cudaGetLastError();
+        return cudaErrorMemoryAllocation;
+    }
+    const dim3 gb(b / RT, nprob, nsplit);
     const size_t smA = ((size_t)std::max(b / 2, 1) * NR + (size_t)8 * 64 * NR) * sizeof(T);
     if (smA > 200 * 1024) return cudaErrorInvalidValue;
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
@@ -618,15 +798,22 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
             k_hnode_t<T, NRV><<<na, 256, smA, s>>>(probs_all, tasks, alist + a_off, nodes, pool, b, nrhs, tbuf);  \
             count_launches(1);                                                                                   \
         }                                                                                                        \
-        ensure_smem((const void*)k_hrows<T, NRV>, sm);                                                         \
-        k_hrows<T, NRV><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf, L,    \
-                                            nrhs, RT);                                                           \
+        ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                      \
+        k_hrows<T, NRV, V><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf, L, \
+                                               nrhs, RT, part);                                                  \
         count_launches(1);                                                                                       \
     }
     if (NR == 1) ACR_HS_LAUNCH(1)
     else if (NR == 4) ACR_HS_LAUNCH(4)
     else ACR_HS_LAUNCH(8)
 #undef ACR_HS_LAUNCH
+    if (part) {
+        const long long tot = (long long)nprob * b * nrhs;
+        const int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
+        k_hrows_reduce<T><<<blocks, 256, 0, s>>>(probs_all + prob_off, nprob, b, nrhs, nsplit, part);
+        count_launches(1);
+        cudaFreeAsync(part, s);
+    }
     return cudaGetLastError();
 }
 

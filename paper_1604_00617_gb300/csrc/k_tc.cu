@@ -5,7 +5,8 @@
 // kernel runs them with tcgen05.mma (kind::tf32, FP32 accumulation in TMEM)
 // at FP32 accuracy by the three-term split  x ~= hi + lo,  hi = x rounded to
 // the nearest TF32 value,  lo = (x - hi) rounded to the nearest TF32 value:
-//     A B  ~=  Ahi Bhi + Ahi Blo + Alo Bhi       (the Alo Blo term is ~2^-22).
+//     A B  ~=  Ahi Bhi + Ahi Blo + Alo Bhi       (the Alo Blo term is ~2^-22;
+// launches that feed cancelling updates, the inversion's, add it as a fourth).
 //
 // One CTA computes one 128 x 128 tile of one problem:
 //   warp 0      TMA producer: A tile (128 rows x 32 k, the operand's natural
@@ -31,11 +32,16 @@ namespace acr {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 32, STAGES = 2;
+constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int TILE_BYTES = BM * BK * 4;  // 16 KB, every operand tile
-// per stage: A_raw, B (hi in place), A_hi, A_lo, B_lo
-constexpr int STAGE_BYTES = 5 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+// Two rings: RAW stages receive the TMA copies (A_raw, B_raw); CONV stages
+// hold the split operands (A_hi, A_lo, B_hi, B_lo) the MMAs read.  A raw
+// stage is released as soon as it is converted, so the copies of later
+// k-steps overlap the conversion and the MMAs of earlier ones.
+constexpr int RAW = 3, CONV = 2;
+constexpr int RAW_BYTES = 2 * TILE_BYTES, CONV_BYTES = 4 * TILE_BYTES;
+constexpr int SMEM_BYTES = RAW * RAW_BYTES + CONV * CONV_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 constexpr int NTHREADS = 192;
 constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait rounds before giving up
 
@@ -123,33 +129,42 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
 
 using namespace tc;
 
+// Problem z: out[:, cols] = alpha * sum_t A_t[:, ka0 : ka0 + kdim] B_t[0 : kdim, cols] + beta * cin,
+// rows 0..b-1 (ld b).  Output column tile tn covers columns ((tn < nskip) ? tn : tn + nshift) * BN,
+// so a launch can leave out a band of column tiles (nskip = INT_MAX: no band).
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps, int b, int tiles_m,
-          int* __restrict__ err) {
+          int* __restrict__ err, int kdim, int ka0, int nskip, int nshift, int lolo) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
-    uint64_t* full = bars;               // [STAGES]
-    uint64_t* conv = bars + STAGES;      // [STAGES]
-    uint64_t* empty = bars + 2 * STAGES; // [STAGES]
-    uint64_t* accb = bars + 3 * STAGES;  // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 1);
+    unsigned char* raw = base;                           // [RAW][A_raw | B_raw]
+    unsigned char* cvt = base + RAW * RAW_BYTES;         // [CONV][A_hi | A_lo | B_hi | B_lo]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(cvt + CONV * CONV_BYTES);
+    uint64_t* full = bars;                  // [RAW]  TMA bytes landed
+    uint64_t* raw_free = bars + RAW;        // [RAW]  converters done with the raw stage
+    uint64_t* conv_full = bars + 2 * RAW;   // [CONV] split operands ready
+    uint64_t* conv_free = conv_full + CONV; // [CONV] MMAs done with them
+    uint64_t* accb = conv_free + CONV;      // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
     __shared__ int s_fail;
 
     // a CTA that gave up on a wait raises *err; later CTAs do no work at all
     if (*reinterpret_cast<volatile int*>(err) != 0) return;
     const TcProb P = probs[blockIdx.y];
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-    const int m0 = tm * BM, n0 = tn * BN;
+    const int m0 = tm * BM, n0 = (tn < nskip ? tn : tn + nshift) * BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kt = b / BK;
+    const int kt = kdim / BK;
     const int niter = P.nterm * kt;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&conv[s], 4);
-            mbar_init(&empty[s], 1);
+        for (int i = 0; i < RAW; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&raw_free[i], 4);
+        }
+        for (int i = 0; i < CONV; ++i) {
+            mbar_init(&conv_full[i], 4);
+            mbar_init(&conv_free[i], 1);
         }
         mbar_init(accb, 1);
         s_fail = 0;
@@ -168,28 +183,26 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
     if (warp == 0) {
         if (lane == 0) {
             for (int it = 0; it < niter; ++it) {
-                const int s = it % STAGES;
-                const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) { s_fail = 1; break; }
-                unsigned char* st = base + s * STAGE_BYTES;
+                const int r = it % RAW;
+                if (it >= RAW && !mbar_wait(&raw_free[r], (uint32_t)(((it / RAW) & 1) ^ 1))) { s_fail = 1; break; }
+                unsigned char* st = raw + r * RAW_BYTES;
                 const int term = it / kt, kq = (it % kt) * BK;
-                mbar_expect_tx(&full[s], 2 * TILE_BYTES);
-                tma_load_3d(st, &maps[P.amap[term]], &full[s], m0, kq, P.az[term]);
-                tma_load_3d(st + TILE_BYTES, &maps[P.bmap[term]], &full[s], kq, n0, P.bz[term]);
+                mbar_expect_tx(&full[r], 2 * TILE_BYTES);
+                tma_load_3d(st, &maps[P.amap[term]], &full[r], m0, ka0 + kq, P.az[term]);
+                tma_load_3d(st + TILE_BYTES, &maps[P.bmap[term]], &full[r], kq, n0, P.bz[term]);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             for (int it = 0; it < niter; ++it) {
-                const int s = it % STAGES;
-                const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                if (!mbar_wait(&conv[s], ph)) { s_fail = 1; break; }
+                const int c = it % CONV;
+                if (!mbar_wait(&conv_full[c], (uint32_t)((it / CONV) & 1))) { s_fail = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                unsigned char* st = base + s * STAGE_BYTES;
-                const uint32_t b_hi = smem_u32(st + TILE_BYTES);
-                const uint32_t a_hi = smem_u32(st + 2 * TILE_BYTES);
-                const uint32_t a_lo = smem_u32(st + 3 * TILE_BYTES);
-                const uint32_t b_lo = smem_u32(st + 4 * TILE_BYTES);
+                unsigned char* cv = cvt + c * CONV_BYTES;
+                const uint32_t a_hi = smem_u32(cv);
+                const uint32_t a_lo = smem_u32(cv + TILE_BYTES);
+                const uint32_t b_hi = smem_u32(cv + 2 * TILE_BYTES);
+                const uint32_t b_lo = smem_u32(cv + 3 * TILE_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint32_t off = kk * 32;  // 8 tf32 along K = 32 bytes inside the swizzle row
@@ -197,8 +210,9 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
                     mma_tf32(tmem_d, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), acc0);
                     mma_tf32(tmem_d, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), 1u);
                     mma_tf32(tmem_d, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), 1u);
+                    if (lolo) mma_tf32(tmem_d, sdesc_sw128(a_lo + off), sdesc_sw128(b_lo + off), 1u);
                 }
-                mma_commit(&empty[s]);
+                mma_commit(&conv_free[c]);
             }
             mma_commit(accb);
         }
@@ -206,44 +220,49 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
         // ---- converters (warps 2..5, 128 threads) --------------------------
         const int t = threadIdx.x - 64;
         for (int it = 0; it < niter; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-            if (!mbar_wait(&full[s], ph)) { s_fail = 1; break; }
-            unsigned char* st = base + s * STAGE_BYTES;
+            const int r = it % RAW, c = it % CONV;
+            if (!mbar_wait(&full[r], (uint32_t)((it / RAW) & 1))) { s_fail = 1; break; }
+            if (it >= CONV && !mbar_wait(&conv_free[c], (uint32_t)(((it / CONV) & 1) ^ 1))) { s_fail = 1; break; }
+            const unsigned char* st = raw + r * RAW_BYTES;
+            unsigned char* cv = cvt + c * CONV_BYTES;
             const float* araw = reinterpret_cast<const float*>(st);   // [k][m], 32 x 128
-            float4* bt = reinterpret_cast<float4*>(st + TILE_BYTES);
-            unsigned char* ahi = st + 2 * TILE_BYTES;
-            unsigned char* alo = st + 3 * TILE_BYTES;
-            float4* blo = reinterpret_cast<float4*>(st + 4 * TILE_BYTES);
+            const float4* braw = reinterpret_cast<const float4*>(st + TILE_BYTES);
+            unsigned char* ahi = cv;
+            unsigned char* alo = cv + TILE_BYTES;
+            float4* bhi = reinterpret_cast<float4*>(cv + 2 * TILE_BYTES);
+            float4* blo = reinterpret_cast<float4*>(cv + 3 * TILE_BYTES);
             // A: row m = t, 8 chunks of 4 k -> K-major swizzled hi / lo
 #pragma unroll
-            for (int c = 0; c < BK / 4; ++c) {
+            for (int q = 0; q < BK / 4; ++q) {
                 float4 h, l;
                 float x;
-                x = araw[(4 * c + 0) * BM + t]; h.x = tf32_hi(x); l.x = tf32_rn(x - h.x);
-                x = araw[(4 * c + 1) * BM + t]; h.y = tf32_hi(x); l.y = tf32_rn(x - h.y);
-                x = araw[(4 * c + 2) * BM + t]; h.z = tf32_hi(x); l.z = tf32_rn(x - h.z);
-                x = araw[(4 * c + 3) * BM + t]; h.w = tf32_hi(x); l.w = tf32_rn(x - h.w);
-                const uint32_t o = sw128_off(t, 4 * c);
+                x = araw[(4 * q + 0) * BM + t]; h.x = tf32_hi(x); l.x = tf32_rn(x - h.x);
+                x = araw[(4 * q + 1) * BM + t]; h.y = tf32_hi(x); l.y = tf32_rn(x - h.y);
+                x = araw[(4 * q + 2) * BM + t]; h.z = tf32_hi(x); l.z = tf32_rn(x - h.z);
+                x = araw[(4 * q + 3) * BM + t]; h.w = tf32_hi(x); l.w = tf32_rn(x - h.w);
+                const uint32_t o = sw128_off(t, 4 * q);
                 *reinterpret_cast<float4*>(ahi + o) = h;
                 *reinterpret_cast<float4*>(alo + o) = l;
             }
-            // B: same layout, split in place
+            // B: already in the K-major swizzled layout; split element-wise
 #pragma unroll
             for (int j = 0; j < TILE_BYTES / 16 / 128; ++j) {
                 const int i = t + j * 128;
-                const float4 v = bt[i];
+                const float4 v = braw[i];
                 float4 h, l;
                 h.x = tf32_hi(v.x); l.x = tf32_rn(v.x - h.x);
                 h.y = tf32_hi(v.y); l.y = tf32_rn(v.y - h.y);
                 h.z = tf32_hi(v.z); l.z = tf32_rn(v.z - h.z);
                 h.w = tf32_hi(v.w); l.w = tf32_rn(v.w - h.w);
-                bt[i] = h;
+                bhi[i] = h;
                 blo[i] = l;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&conv[s]);
+            if (lane == 0) {
+                mbar_arrive(&raw_free[r]);
+                mbar_arrive(&conv_full[c]);
+            }
         }
         // ---- epilogue ---------------------------------------------------------
         const bool ok = mbar_wait(accb, 0);
@@ -266,14 +285,20 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (ok && row < b) {
+                // all 32 loads first: out may alias cin, so a load placed after
+                // a store could not be moved ahead of it, and the chunk would
+                // pay one memory round trip per column
+                const size_t o0 = (size_t)row + (size_t)(n0 + cj * 32) * b;
+                float cv[32];
+                if (P.cin) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int col = n0 + cj * 32 + c;
-                    const size_t o = (size_t)row + (size_t)col * b;
-                    float v = P.alpha * __uint_as_float(r[c]);
-                    if (P.cin) v += P.beta * P.cin[o];
-                    P.out[o] = v;
+                    for (int c = 0; c < 32; ++c) cv[c] = P.cin[o0 + (size_t)c * b];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) cv[c] = 0.f;
                 }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) P.out[o0 + (size_t)c * b] = P.alpha * __uint_as_float(r[c]) + P.beta * cv[c];
             }
         }
     }
@@ -314,11 +339,12 @@ bool tc_supported(int b) { return b >= 128 && b % 128 == 0 && encode_fn() != nul
 
 // role 0: left operand (column-major rows are the MMA's M): box 128 rows x 32 k, no swizzle.
 // role 1: right operand (K contiguous): box 32 k x 128 cols, 128-byte swizzle.
-int tc_encode_map(void* map_out, const float* base, int b, int count, int role) {
+// `count` matrices of d0 (contiguous) x d1 FP32 elements, one after another.
+int tc_encode_map_dims(void* map_out, const float* base, int d0, int d1, int count, int role) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return -1;
-    cuuint64_t dims[3] = {(cuuint64_t)b, (cuuint64_t)b, (cuuint64_t)(count > 0 ? count : 1)};
-    cuuint64_t strides[2] = {(cuuint64_t)b * 4, (cuuint64_t)b * b * 4};
+    cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)(count > 0 ? count : 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4};
     cuuint32_t box[3] = {role == 0 ? (cuuint32_t)BM : (cuuint32_t)BK, role == 0 ? (cuuint32_t)BK : (cuuint32_t)BN, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -328,16 +354,27 @@ int tc_encode_map(void* map_out, const float* base, int b, int count, int role) 
     return r == CUDA_SUCCESS ? 0 : -2;
 }
 
+int tc_encode_map(void* map_out, const float* base, int b, int count, int role) {
+    return tc_encode_map_dims(map_out, base, b, b, count, role);
+}
+
 size_t tc_map_bytes() { return sizeof(CUtensorMap); }
 
-cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s) {
-    if (nprob <= 0) return cudaSuccess;
+cudaError_t gemm_tc_ex(const TcProb* d_probs, int nprob, const void* d_maps, int b, int kdim, int ka0,
+                       int tiles_n, int nskip, int nshift, int lolo, int* d_err, cudaStream_t s) {
+    if (nprob <= 0 || tiles_n <= 0) return cudaSuccess;
+    if (b % BM || kdim % BK || kdim <= 0 || ka0 % BK) return cudaErrorInvalidValue;
     ensure_smem((const void*)k_gemm_tc, SMEM_BYTES);
-    const int tiles_m = b / BM, tiles_n = b / BN;
+    const int tiles_m = b / BM;
     dim3 g(tiles_m * tiles_n, nprob);
-    k_gemm_tc<<<g, NTHREADS, SMEM_BYTES, s>>>(d_probs, static_cast<const CUtensorMap*>(d_maps), b, tiles_m, d_err);
+    k_gemm_tc<<<g, NTHREADS, SMEM_BYTES, s>>>(d_probs, static_cast<const CUtensorMap*>(d_maps), b, tiles_m, d_err,
+                                              kdim, ka0, nskip, nshift, lolo);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t gemm_tc(const TcProb* d_probs, int nprob, const void* d_maps, int b, int* d_err, cudaStream_t s) {
+    return gemm_tc_ex(d_probs, nprob, d_maps, b, b, 0, b / BN, 1 << 30, 0, 0, d_err, s);
 }
 
 }  // namespace acr
