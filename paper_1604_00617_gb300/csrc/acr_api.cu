@@ -876,6 +876,10 @@ struct SweepPlan {
     std::vector<size_t> task_start;  // first task of every problem (+ total)
     DevBuf halist;                   // indices of the low-rank tasks
     std::vector<size_t> a_start;     // first low-rank task (in halist) of every problem
+    DevBuf hterms;                   // compressed terms with low-rank nodes: (problem << 1) | term
+    std::vector<size_t> t_start;     // first entry (in hterms) of every problem
+    int rkmax = 0;                   // largest rank of a low-rank node
+    std::vector<int> pwmax;          // widest row tile of every problem
     bool hodlr = false;
     std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
     int nrhs = 0;
@@ -1045,9 +1049,13 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
             HSweepProb<T>& q = hp[pi];
             for (int t = 0; t < 2; ++t) {
                 q.tbase[t] = -1;
+                q.node_base[t] = 0;
+                q.leaf_off[t] = 0;
                 if (q.dg[t] || q.blk[t] < 0 || !q.x[t]) continue;
                 q.tbase[t] = (int)tasks.size();
                 const HBlk& hbk = h->hblks_host[q.blk[t]];
+                q.node_base[t] = hbk.node_base;
+                q.leaf_off[t] = hbk.leaf_off;
                 for (int nu = 0; nu < h->npb; ++nu) {
                     int l = 1;
                     while (((1 << (l + 1)) - 2) <= nu) ++l;
@@ -1076,6 +1084,45 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
                 if (tasks[ti].toff >= 0) alist.push_back((int)ti);
         }
         sp.a_start[hp.size()] = alist.size();
+        // pass A per compressed term: the terms that own a low-rank node
+        std::vector<int> terms;
+        sp.t_start.assign(hp.size() + 1, 0);
+        for (size_t pi = 0; pi < hp.size(); ++pi) {
+            sp.t_start[pi] = terms.size();
+            for (int t = 0; t < 2; ++t) {
+                const int tb = hp[pi].tbase[t];
+                if (tb < 0) continue;
+                bool any = false;
+                for (int nu = 0; nu < h->npb; ++nu) any |= tasks[(size_t)tb + nu].toff >= 0;
+                if (any) terms.push_back(((int)pi << 1) | t);
+            }
+        }
+        sp.t_start[hp.size()] = terms.size();
+        sp.rkmax = 0;
+        for (const HNode& hn : h->hnodes_host) sp.rkmax = std::max(sp.rkmax, hn.rank);
+        // widest row tile of every problem: leaf + per tree level the widest
+        // node (rank, or the node size when dense)
+        std::vector<int> bw(h->hblks_host.size(), 0);
+        for (size_t g = 0; g < bw.size(); ++g) {
+            int w = h->leaf;
+            for (int l = 1; l <= h->hL; ++l) {
+                const int sz = b >> l;
+                int m = 0;
+                for (int ni = 0; ni < (1 << l); ++ni) {
+                    const HNode& hn = h->hnodes_host[(size_t)h->hblks_host[g].node_base + (1 << l) - 2 + ni];
+                    m = std::max(m, hn.rank < 0 ? sz : hn.rank);
+                }
+                w += m;
+            }
+            bw[g] = w;
+        }
+        sp.pwmax.assign(hp.size(), 0);
+        for (size_t pi = 0; pi < hp.size(); ++pi)
+            for (int t = 0; t < 2; ++t)
+                if (hp[pi].blk[t] >= 0 && !hp[pi].dg[t]) sp.pwmax[pi] = std::max(sp.pwmax[pi], bw[hp[pi].blk[t]]);
+        CK(sp.hterms.alloc(std::max<size_t>(1, terms.size()) * sizeof(int), s));
+        if (!terms.empty())
+            CK(cudaMemcpyAsync(sp.hterms.p, terms.data(), terms.size() * sizeof(int), cudaMemcpyHostToDevice, s));
         CK(sp.halist.alloc(std::max<size_t>(1, alist.size()) * sizeof(int), s));
         if (!alist.empty())
             CK(cudaMemcpyAsync(sp.halist.p, alist.data(), alist.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1136,10 +1183,14 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
         const HTask* tk = sp.htasks.template as<HTask>();
         T* tb = sp.htbuf.template as<T>();
         const int* al = sp.halist.template as<int>();
+        const int* tl = sp.hterms.template as<int>();
         auto seg = [&](size_t off, size_t cnt) -> cudaError_t {
             const size_t a0 = sp.a_start[off], a1 = sp.a_start[off + cnt];
-            return hsweep<T>(hq, (int)off, (int)cnt, tk, al, (int)a0, (int)(a1 - a0), tb, hb, hn, pool, b, h->leaf,
-                             h->hL, nrhs, s);
+            const size_t t0 = sp.t_start[off], t1 = sp.t_start[off + cnt];
+            int wmax = 0;
+            for (size_t pi = off; pi < off + cnt; ++pi) wmax = std::max(wmax, sp.pwmax[pi]);
+            return hsweep<T>(hq, (int)off, (int)cnt, tk, al, (int)a0, (int)(a1 - a0), tl + t0, (int)(t1 - t0),
+                             sp.rkmax, wmax, tb, hb, hn, pool, b, h->leaf, h->hL, nrhs, s);
         };
         for (int t = 0; t <= T_; ++t) {
             CK(seg(sp.fw_g_off[t], sp.fw_g_cnt[t]));

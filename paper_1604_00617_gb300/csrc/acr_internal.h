@@ -158,8 +158,14 @@ struct HSweepProb {
     const T* dg[2];
     int blk[2];
     int tbase[2];  // first task (of its npb node tasks) of each compressed term
+    int node_base[2];         // the blocks' first node and leaves (copies of
+    long long leaf_off[2];    // their HBlk, saving the kernel a dependent load)
     T alpha;
 };
+// Pass A runs either per low-rank node (alist: task indices) or per compressed
+// term (terms: (problem << 1) | term, rkmax: the largest node rank).  wmax:
+// the widest row tile of the launch (leaf plus the node widths of every tree
+// level), 0 if unknown; narrow launches run one warp per row tile.
 // One node product of the apply: t = V^T x (pass A).  toff: offset of t
 // (rank x nrhs, column-major) in the product buffer; -1 when the node is dense
 // or of rank 0.
@@ -187,8 +193,8 @@ cudaError_t pack_leaves(const T* const* blocks, const long long* leaf_off, int n
 // products (pass A writes, pass B reads).
 template <class T>
 cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, const HTask* tasks, const int* alist,
-                   int a_off, int na, T* tbuf, const HBlk* blks, const HNode* nodes, const T* pool, int b, int leaf,
-                   int L, int nrhs, cudaStream_t s);
+                   int a_off, int na, const int* terms, int nterms, int rkmax, int wmax, T* tbuf, const HBlk* blks,
+                   const HNode* nodes, const T* pool, int b, int leaf, int L, int nrhs, cudaStream_t s);
 
 // --- batched block x multi-vector (solve sweeps, dense FP64 residual) ----
 template <class T>

@@ -1096,19 +1096,30 @@ k_sweep_vec(const SweepProb<T>* __restrict__ probs, int b, int nrhs, T* __restri
                 continue;
             }
             __syncthreads();
-            for (int i = tid; i < kn * NR; i += NT) {
-                const int cl = i % kn, q = i / kn, c = kbeg + cl;
-                T xv = T(0);
-                if (q < nq) {
-                    const size_t o = c + (size_t)(q0 + q) * P.ldx;
-                    if (comb) {
-                        xv = P.sx[0][c] * X[o];
-                        if (P.x[1]) xv += P.sx[1][c] * P.x[1][o];
-                    } else {
-                        xv = X[o];
+            // 8 loads in flight per thread before their stores (a store right
+            // after each load would expose one memory latency per element)
+            for (int i0 = tid; i0 < kn * NR; i0 += 8 * NT) {
+                T xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * NT;
+                    xv[u] = T(0);
+                    const int cl = i % kn, q = i / kn, c = kbeg + cl;
+                    if (i < kn * NR && q < nq) {
+                        const size_t o = c + (size_t)(q0 + q) * P.ldx;
+                        if (comb) {
+                            xv[u] = P.sx[0][c] * X[o];
+                            if (P.x[1]) xv[u] += P.sx[1][c] * P.x[1][o];
+                        } else {
+                            xv[u] = X[o];
+                        }
                     }
                 }
-                xs[cl * NR + q] = xv;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * NT;
+                    if (i < kn * NR) xs[(i % kn) * NR + i / kn] = xv[u];
+                }
             }
             __syncthreads();
             if (live) {
@@ -1130,20 +1141,22 @@ k_sweep_vec(const SweepProb<T>* __restrict__ probs, int b, int nrhs, T* __restri
 #pragma unroll
             for (int q = 0; q < NR; ++q) red[g][rg * V + v][q] = acc[v][q];
         __syncthreads();
-        for (int i = tid; i < RT * NR; i += NT) {
-            const int r = i % RT, q = i / RT;
-            const int gr = row0 + r;
-            if (gr < b && q < nq) {
+        constexpr int PER = (RT * NR + NT - 1) / NT;  // outputs per thread
+        T cv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {  // all cin loads before the stores
+            const int i = tid + u * NT, r = i % RT, q = i / RT, gr = row0 + r;
+            cv[u] = (!part && P.cin && i < RT * NR && gr < b && q < nq) ? P.cin[gr + (size_t)(q0 + q) * P.ldc] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = tid + u * NT, r = i % RT, q = i / RT, gr = row0 + r;
+            if (i < RT * NR && gr < b && q < nq) {
                 T sum = T(0);
 #pragma unroll
                 for (int gg = 0; gg < KG; ++gg) sum += red[gg][r][q];
-                if (part) {
-                    part[(((size_t)z * gridDim.y + blockIdx.y) * b + gr) * nrhs + q0 + q] = sum;
-                } else {
-                    T o = P.alpha * sum;
-                    if (P.cin) o += P.cin[gr + (size_t)(q0 + q) * P.ldc];
-                    P.out[gr + (size_t)(q0 + q) * P.ldo] = o;
-                }
+                if (part) part[(((size_t)z * gridDim.y + blockIdx.y) * b + gr) * nrhs + q0 + q] = sum;
+                else P.out[gr + (size_t)(q0 + q) * P.ldo] = P.alpha * sum + cv[u];
             }
         }
         __syncthreads();

@@ -537,9 +537,18 @@ k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tas
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         __syncthreads();
-        for (int i = tid; i < s * NR; i += 256) {
-            const int c = i % s, q = i / s;
-            xs[c * NR + q] = q < nq ? xval(P, tk.term, c0 + c, q0 + q) : T(0);
+        for (int i0 = tid; i0 < s * NR; i0 += 8 * 256) {  // 8 loads in flight per thread
+            T xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 256, c = i % s, q = i / s;
+                xv[u] = (i < s * NR && q < nq) ? xval(P, tk.term, c0 + c, q0 + q) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 256;
+                if (i < s * NR) xs[(i % s) * NR + i / s] = xv[u];
+            }
         }
         __syncthreads();
         for (int ib = 0; ib < rk; ib += 32) {  // rank indices ib + i0 (two passes when rk > 32)
@@ -571,6 +580,111 @@ k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tas
 #pragma unroll
                 for (int w = 0; w < 8; ++w) sum += red[((size_t)w * 64 + ii) * NR + q];
                 tbuf[tk.toff + ii + (size_t)(q0 + q) * rk] = sum;
+            }
+        }
+    }
+}
+
+// Pass A, one CTA per compressed term (problem, term): t_node = V^T x[cols]
+// for every low-rank node of the block.  The term's whole x (b x NR) is
+// staged once; every node is cut into items of CH rows of V (one tree level
+// spans b / CH items), the warps take the items round-robin and write each
+// item's partial t (rank x NR) to shared memory, and the partials of a node
+// are summed in item order.
+template <class T, int NR>
+__global__ void __launch_bounds__(256)
+k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms, const HTask* __restrict__ tasks,
+         const HNode* __restrict__ nodes, const T* __restrict__ pool, int b, int L, int CH, int nrhs, int rkmax,
+         T* __restrict__ tbuf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);    // b x NR
+    T* part = xs + (size_t)b * NR;             // items x rkmax x NR
+    // the block's node table, read once: rank (<= 0: no product), pool offset,
+    // offset of t in tbuf
+    __shared__ int s_rk[254];
+    __shared__ long long s_off[254], s_toff[254];
+    const int e = terms[blockIdx.x];
+    const int p = e >> 1, term = e & 1;
+    const HSweepProb<T>& P = probs[p];
+    const int tb = P.tbase[term];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int per_level = b / CH, nitems = L * per_level;
+    const int npb = (1 << (L + 1)) - 2;
+    for (int i = tid; i < npb; i += 256) {
+        const HTask tk = tasks[tb + i];
+        const HNode hn = nodes[tk.node];
+        s_toff[i] = tk.toff;
+        s_rk[i] = tk.toff >= 0 ? hn.rank : 0;
+        s_off[i] = hn.off;
+    }
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = min(NR, nrhs - q0);
+        __syncthreads();
+        for (int i0 = tid; i0 < b * NR; i0 += 8 * 256) {  // 8 loads in flight per thread
+            T xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 256, c = i % b, q = i / b;
+                xv[u] = (i < b * NR && q < nq) ? xval(P, term, c, q0 + q) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 256;
+                if (i < b * NR) xs[(i % b) * NR + i / b] = xv[u];
+            }
+        }
+        __syncthreads();
+        for (int it = warp; it < nitems; it += 8) {
+            const int l = 1 + it / per_level, u = it % per_level;
+            const int sz = b >> l, cpn = sz / CH;  // items per node
+            const int ni = u / cpn, cc = u % cpn;
+            const int nu = (1 << l) - 2 + ni;
+            const int rk = s_rk[nu];
+            if (rk <= 0) continue;
+            const T* Vt = pool + s_off[nu] + (size_t)sz * rk;  // rank x sz, rank values of a row contiguous
+            const int c0 = (ni ^ 1) * sz;
+            const int rlo = rk < 32 ? rk : 32;
+            int rp = 1;
+            while (rp < rlo) rp <<= 1;
+            const int G = 32 / rp, g = lane / rp, i0 = lane % rp;
+            const int j0 = cc * CH, j1 = j0 + CH;
+            for (int ib = 0; ib < rk; ib += 32) {
+                const int ii = ib + i0;
+                const bool live = i0 < rp && ii < rk;
+                T acc[NR];
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                if (live) {
+#pragma unroll 4
+                    for (int j = j0 + g; j < j1; j += G) {
+                        const T v = Vt[ii + (size_t)j * rk];
+                        const T* xr = xs + (size_t)(c0 + j) * NR;
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = fma(v, xr[q], acc[q]);
+                    }
+                }
+                for (int o = rp; o < 32; o <<= 1)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (g == 0 && live)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) part[((size_t)it * rkmax + ii) * NR + q] = acc[q];
+            }
+        }
+        __syncthreads();
+        // node sums in item order: one warp per node, lanes over (rank index, column)
+        for (int nu = warp; nu < npb; nu += 8) {
+            const int rk = s_rk[nu];
+            if (rk <= 0) continue;
+            int l = 1;
+            while (((1 << (l + 1)) - 2) <= nu) ++l;
+            const int ni = nu - ((1 << l) - 2), cpn = (b >> l) / CH;
+            const int it0 = (l - 1) * per_level + ni * cpn;
+            for (int o = lane; o < rk * nq; o += 32) {
+                const int ii = o % rk, q = o / rk;
+                T sum = T(0);
+                for (int cc = 0; cc < cpn; ++cc) sum += part[((size_t)(it0 + cc) * rkmax + ii) * NR + q];
+                tbuf[s_toff[nu] + ii + (size_t)(q0 + q) * rk] = sum;
             }
         }
     }
@@ -613,6 +727,14 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
     const int nz = gridDim.z, z = blockIdx.z;
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
+        // this thread's final outputs (i = tid, tid + 256 < RT * NR): cin early
+        T cpre[2] = {T(0), T(0)};
+        if (!part && P.cin)
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const int i = tid + k2 * 256, r = i % RT, q = i / RT;
+                if (i < RT * NR && q < nq) cpre[k2] = P.cin[R0 + r + (size_t)(q0 + q) * P.ldc];
+            }
         T acc[V][NR];
 #pragma unroll
         for (int v = 0; v < V; ++v)
@@ -632,7 +754,6 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
             if (P.blk[t] < 0) continue;
             __syncthreads();  // xs and the segment table are free
             if (warp == 0) {
-                const HBlk B = blks[P.blk[t]];
                 const int li = R0 / leaf;
                 // lane 0: the leaf; lane l (1..L): the node of tree level l
                 int kind = -1, ld = 0, ncol = 0, rk = 0;
@@ -640,13 +761,15 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
                 long long src = 0;
                 if (lane == 0) {
                     kind = 0;
-                    ptr = pool + B.leaf_off + (size_t)li * leaf * leaf + (R0 - li * leaf);
+                    ptr = pool + P.leaf_off[t] + (size_t)li * leaf * leaf + (R0 - li * leaf);
                     ld = leaf;
                     ncol = leaf;
                     src = (long long)li * leaf;
                 } else if (lane <= L) {
                     const int l = lane, sz = b >> l, ni = R0 / sz;
-                    const HNode hn = nodes[B.node_base + (1 << l) - 2 + ni];
+                    // both loads issued before either is used
+                    const HNode hn = nodes[P.node_base[t] + (1 << l) - 2 + ni];
+                    const long long toff = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
                     const int r0 = ni * sz;
                     ld = sz;
                     ptr = pool + hn.off + (R0 - r0);
@@ -658,7 +781,7 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
                         kind = 1;
                         ncol = hn.rank;
                         rk = hn.rank;
-                        src = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
+                        src = toff;
                     }
                 }
                 // exclusive prefix of the widths over lanes 0..L, in lane order
@@ -685,17 +808,28 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
             const int J0 = min(Wall, z * JS), J1 = min(Wall, J0 + JS);
             const int W = J1 - J0;
             // stage the inputs of those columns: xs[(j - J0) * NR + q]
-            for (int i = tid; i < W * NR; i += 256) {
-                const int j = J0 + i % W, q = i / W;
-                int sg = 0;
-                while (s_cs[sg + 1] <= j) ++sg;
-                const int c = j - s_cs[sg];
-                T xv = T(0);
-                if (q < nq) {
-                    if (s_kind[sg] == 1) xv = tbuf[s_src[sg] + c + (size_t)(q0 + q) * s_rk[sg]];
-                    else xv = xval(P, t, (int)s_src[sg] + c, q0 + q);
+            for (int i0 = tid; i0 < W * NR; i0 += 4 * 256) {  // 4 loads in flight per thread
+                T xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * 256;
+                    xv[u] = T(0);
+                    if (i < W * NR) {
+                        const int j = J0 + i % W, q = i / W;
+                        int sg = 0;
+                        while (s_cs[sg + 1] <= j) ++sg;
+                        const int c = j - s_cs[sg];
+                        if (q < nq) {
+                            if (s_kind[sg] == 1) xv[u] = tbuf[s_src[sg] + c + (size_t)(q0 + q) * s_rk[sg]];
+                            else xv[u] = xval(P, t, (int)s_src[sg] + c, q0 + q);
+                        }
+                    }
                 }
-                xs[(j - J0) * NR + q] = xv;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * 256;
+                    if (i < W * NR) xs[(i % W) * NR + i / W] = xv[u];
+                }
             }
             __syncthreads();
             for (int sg = 0; sg <= L; ++sg) {
@@ -725,20 +859,164 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
 #pragma unroll
             for (int q = 0; q < NR; ++q) red[((size_t)g * RT + rg * V + v) * NR + q] = acc[v][q];
         __syncthreads();
-        for (int i = tid; i < RT * NR; i += 256) {
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {
+            const int i = tid + k2 * 256;
             const int r = i % RT, q = i / RT;
-            if (q < nq) {
+            if (i < RT * NR && q < nq) {
                 T sum = T(0);
                 for (int gg = 0; gg < KG; ++gg) sum += red[((size_t)gg * RT + r) * NR + q];
                 if (part) {
                     part[(((size_t)z * gridDim.y + blockIdx.y) * b + R0 + r) * nrhs + q0 + q] = sum;
                 } else {
                     T o = P.alpha * sum;
-                    if (P.cin) o += P.cin[R0 + r + (size_t)(q0 + q) * P.ldc];
+                    if (P.cin) o += cpre[k2];
                     P.out[R0 + r + (size_t)(q0 + q) * P.ldo] = o;
                 }
             }
         }
+    }
+}
+
+// Pass B for launches whose tiles are narrow (at most wmax concatenated
+// columns): one warp per row tile, independent of the other warps of its
+// CTA.  Lanes = RT/V row groups x (32 / (RT/V)) column groups; the warp stages
+// its inputs in its own slice of shared memory, streams the rows with 16-byte
+// loads, adds the column groups by shuffles and writes the tile.
+template <class T, int NR, int V>
+__global__ void __launch_bounds__(256)
+k_hrows_w(const HSweepProb<T>* __restrict__ probs, const HNode* __restrict__ nodes, const HTask* __restrict__ tasks,
+          const T* __restrict__ tbuf, const T* __restrict__ pool, int b, int leaf, int L, int nrhs, int RT,
+          int wmax) {
+    using VT = typename HVec<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* xs = reinterpret_cast<T*>(smem_raw) + (size_t)warp * wmax * NR;  // this warp's [wmax][NR]
+    const int tiles = b / RT;
+    const int tile = blockIdx.x * 8 + warp;
+    if (tile >= tiles) return;
+    const HSweepProb<T>& P = probs[blockIdx.y];
+    const int R0 = tile * RT;
+    const int RG = RT / V, KG = 32 / RG;
+    const int rg = lane % RG, g = lane / RG;
+    const int row = R0 + rg * V;
+    for (int q0 = 0; q0 < nrhs; q0 += NR) {
+        const int nq = min(NR, nrhs - q0);
+        T acc[V][NR];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[v][q] = T(0);
+        for (int t = 0; t < 2; ++t) {
+            if (!P.x[t]) continue;
+            if (P.dg[t]) {
+                if (g == 0)
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+                            if (q < nq) acc[v][q] += P.dg[t][row + v] * P.x[t][row + v + (size_t)(q0 + q) * P.ldx];
+                continue;
+            }
+            if (P.blk[t] < 0) continue;
+            // segment table in registers of lanes 0..L: lane 0 the leaf, lane l the level-l node
+            const int li = R0 / leaf;
+            int kind = -1, ld = 0, ncol = 0, rk = 0;
+            long long off = 0, src = 0;
+            if (lane == 0) {
+                kind = 0;
+                off = P.leaf_off[t] + (long long)li * leaf * leaf + (R0 - li * leaf);
+                ld = leaf;
+                ncol = leaf;
+                src = (long long)li * leaf;
+            } else if (lane <= L) {
+                const int l = lane, sz = b >> l, ni = R0 / sz;
+                const HNode hn = nodes[P.node_base[t] + (1 << l) - 2 + ni];
+                const long long toff = tasks[P.tbase[t] + (1 << l) - 2 + ni].toff;
+                ld = sz;
+                off = hn.off + (R0 - ni * sz);
+                if (hn.rank < 0) {
+                    kind = 0;
+                    ncol = sz;
+                    src = (long long)(ni ^ 1) * sz;
+                } else if (hn.rank > 0) {
+                    kind = 1;
+                    ncol = hn.rank;
+                    rk = hn.rank;
+                    src = toff;
+                }
+            }
+            int cs = ncol;  // inclusive prefix of the widths
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, cs, o);
+                if (lane >= o) cs += y;
+            }
+            const int W = __shfl_sync(0xffffffffu, cs, L);
+            __syncwarp();  // the previous term's reads of xs are done
+            // stage: segment sg holds columns [cs_sg - ncol_sg, cs_sg)
+            for (int sg = 0; sg <= L; ++sg) {
+                const int e1 = __shfl_sync(0xffffffffu, cs, sg);
+                const int n1 = __shfl_sync(0xffffffffu, ncol, sg);
+                const int k1 = __shfl_sync(0xffffffffu, kind, sg);
+                const int r1 = __shfl_sync(0xffffffffu, rk, sg);
+                const long long s1 = __shfl_sync(0xffffffffu, src, sg);
+                const int c0 = e1 - n1;
+                for (int i0 = lane; i0 < n1 * NR; i0 += 8 * 32) {  // 8 loads in flight per lane
+                    T xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * 32, c = i % n1, q = i / n1;
+                        xv[u] = T(0);
+                        if (i < n1 * NR && q < nq)
+                            xv[u] = (k1 == 1) ? tbuf[s1 + c + (size_t)(q0 + q) * r1] : xval(P, t, (int)s1 + c, q0 + q);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + u * 32;
+                        if (i < n1 * NR) xs[(c0 + i % n1) * NR + i / n1] = xv[u];
+                    }
+                }
+            }
+            __syncwarp();
+            for (int sg = 0; sg <= L; ++sg) {
+                const int e1 = __shfl_sync(0xffffffffu, cs, sg);
+                const int n1 = __shfl_sync(0xffffffffu, ncol, sg);
+                const int l1 = __shfl_sync(0xffffffffu, ld, sg);
+                const long long o1 = __shfl_sync(0xffffffffu, off, sg);
+                if (n1 <= 0) continue;
+                const int c0 = e1 - n1;
+                const T* __restrict__ mp = pool + o1 + rg * V;
+#pragma unroll 4
+                for (int c = g; c < n1; c += KG) {
+                    const VT mv = *reinterpret_cast<const VT*>(mp + (size_t)c * l1);
+                    const T* mvp = reinterpret_cast<const T*>(&mv);
+                    const T* xr = xs + (size_t)(c0 + c) * NR;
+#pragma unroll
+                    for (int q = 0; q < NR; ++q)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v][q] = fma(mvp[v], xr[q], acc[v][q]);
+                }
+            }
+            (void)W;
+        }
+        // sum the column groups (lanes rg, rg + RG, ...) in a fixed order
+        for (int o = RG; o < 32; o <<= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[v][q] += __shfl_xor_sync(0xffffffffu, acc[v][q], o);
+        if (g == 0)
+#pragma unroll
+            for (int q = 0; q < NR; ++q)
+                if (q < nq)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const size_t r = (size_t)row + v;
+                        T o = P.alpha * acc[v][q];
+                        if (P.cin) o += P.cin[r + (size_t)(q0 + q) * P.ldc];
+                        P.out[r + (size_t)(q0 + q) * P.ldo] = o;
+                    }
     }
 }
 
@@ -763,8 +1041,8 @@ __global__ void k_hrows_reduce(const HSweepProb<T>* __restrict__ probs, int npro
 
 template <class T>
 cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, const HTask* tasks, const int* alist,
-                   int a_off, int na, T* tbuf, const HBlk* blks, const HNode* nodes, const T* pool, int b, int leaf,
-                   int L, int nrhs, cudaStream_t s) {
+                   int a_off, int na, const int* terms, int nterms, int rkmax, int wmax, T* tbuf, const HBlk* blks,
+                   const HNode* nodes, const T* pool, int b, int leaf, int L, int nrhs, cudaStream_t s) {
     if (nprob <= 0 || nrhs <= 0) return cudaSuccess;
     const int NR = nrhs == 1 ? 1 : (nrhs <= 4 ? 4 : 8);
     // row tile: the largest power of two (<= 64) dividing the leaf, so that a
@@ -776,10 +1054,13 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     // xs holds the staged inputs (<= b columns), then the KG x RT group sums
     const size_t sm = (size_t)std::max(b, 256 * V) * NR * sizeof(T);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
+    // narrow tiles (the low reduction levels): one warp per tile
+    const bool by_warp = wmax > 0 && wmax <= 256 && L <= 31 && 32 % (RT / V) == 0;
+    const size_t smW = (size_t)8 * std::max(wmax, 1) * NR * sizeof(T);
     // few row tiles: split each tile's columns over CTAs so that every SM streams
     int nsplit = 1;
     const long long tiles = (long long)nprob * (b / RT);
-    if (tiles < 2 * 152) {
+    if (!by_warp && tiles < 2 * 152) {
         nsplit = (int)((4 * 152 + tiles - 1) / tiles);
         nsplit = std::min(nsplit, std::max(1, b / 64));
     }
@@ -791,16 +1072,36 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     const dim3 gb(b / RT, nprob, nsplit);
     const size_t smA = ((size_t)std::max(b / 2, 1) * NR + (size_t)8 * 64 * NR) * sizeof(T);
     if (smA > 200 * 1024) return cudaErrorInvalidValue;
+    // pass A per term when its partials fit: items of CH rows (CH divides every node size)
+    const int CH = std::min(64, leaf);
+    auto smt = [&](int nr) { return ((size_t)b * nr + (size_t)L * (b / CH) * std::max(rkmax, 1) * nr) * sizeof(T); };
+    const size_t smT = smt(NR);
+    // decided at the widest chunk, so that every column count takes the same
+    // kernel (and summation order)
+    const bool per_term = terms != nullptr && rkmax <= 64 && L <= 6 && smt(8) <= 160 * 1024;
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
     {                                                                                                            \
-        if (na > 0) {                                                                                            \
+        if (per_term) {                                                                                          \
+            if (nterms > 0) {                                                                                    \
+                ensure_smem((const void*)k_hnodes<T, NRV>, smT);                                               \
+                k_hnodes<T, NRV><<<nterms, 256, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH, nrhs,   \
+                                                          std::max(rkmax, 1), tbuf);                             \
+                count_launches(1);                                                                               \
+            }                                                                                                    \
+        } else if (na > 0) {                                                                                     \
             ensure_smem((const void*)k_hnode_t<T, NRV>, smA);                                                  \
             k_hnode_t<T, NRV><<<na, 256, smA, s>>>(probs_all, tasks, alist + a_off, nodes, pool, b, nrhs, tbuf);  \
             count_launches(1);                                                                                   \
         }                                                                                                        \
-        ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                      \
-        k_hrows<T, NRV, V><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf, L, \
-                                               nrhs, RT, part);                                                  \
+        if (by_warp) {                                                                                           \
+            ensure_smem((const void*)k_hrows_w<T, NRV, V>, smW);                                               \
+            k_hrows_w<T, NRV, V><<<dim3((b / RT + 7) / 8, nprob), 256, smW, s>>>(                              \
+                probs_all + prob_off, nodes, tasks, tbuf, pool, b, leaf, L, nrhs, RT, std::max(wmax, 1));        \
+        } else {                                                                                                 \
+            ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                  \
+            k_hrows<T, NRV, V><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf,\
+                                                   L, nrhs, RT, part);                                           \
+        }                                                                                                        \
         count_launches(1);                                                                                       \
     }
     if (NR == 1) ACR_HS_LAUNCH(1)
@@ -826,8 +1127,9 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     template cudaError_t pack_nodes<T>(const HNode*, int, int, const T*, const T*, const T* const*, int, int, int, \
                                        T*, cudaStream_t);                                                         \
     template cudaError_t pack_leaves<T>(const T* const*, const long long*, int, int, int, T*, cudaStream_t);       \
-    template cudaError_t hsweep<T>(const HSweepProb<T>*, int, int, const HTask*, const int*, int, int, T*,        \
-                                   const HBlk*, const HNode*, const T*, int, int, int, int, cudaStream_t);
+    template cudaError_t hsweep<T>(const HSweepProb<T>*, int, int, const HTask*, const int*, int, int, const int*, \
+                                   int, int, int, T*, const HBlk*, const HNode*, const T*, int, int, int, int,  \
+                                   cudaStream_t);
 ACR_HODLR_INST(float)
 ACR_HODLR_INST(double)
 
