@@ -246,7 +246,10 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
 // them, KB values each, in registers).  Per pivot: block arg-max of the pivot
 // column, the owners of rows k and p publish them through shared memory, then
 // every thread applies the GJ step to its own rows.  Same arithmetic as
-// k_gj_panel.
+// k_gj_panel.  The pivot loop is not unrolled (a straight-line copy of all KB
+// steps does not fit the instruction cache): instead every step leaves each
+// row rotated left by one column, so the pivot column is always v[.][0] and
+// register indices stay static; after KB steps the columns are back in order.
 template <class T, int NT, int RPT, int KB>
 __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b, int k0,
                                                      int* __restrict__ pivs, int* __restrict__ info,
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     }
     const T tiny = T(16) * Lim<T>::eps() * amax_in[blockIdx.x];
     int first_bad = 0;
-#pragma unroll
+#pragma unroll 1
     for (int kk = 0; kk < KB; ++kk) {
         const int k = k0 + kk;
         T val = T(-1);
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
             if (r >= k && r < b) {
-                const T a = tabs(v[i][kk]);
+                const T a = tabs(v[i][0]);
                 if (a > val) { val = a; idx = r; }
             }
         }
@@ -298,25 +301,26 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
             }
         }
         __syncthreads();
-        const T inv = bad ? T(1) : T(1) / sp[kk];
+        const T inv = bad ? T(1) : T(1) / sp[0];
+        // column c of this step is stored at c - 1 afterwards (the pivot
+        // column, c = 0, moves to KB - 1)
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
             if (r >= b) continue;
             if (r == k) {
 #pragma unroll
-                for (int c = 0; c < KB; ++c) v[i][c] = (c == kk) ? inv : sp[c] * inv;
+                for (int c = 0; c < KB - 1; ++c) v[i][c] = sp[c + 1] * inv;
+                v[i][KB - 1] = inv;
             } else {
                 if (r == p) {
 #pragma unroll
                     for (int c = 0; c < KB; ++c) v[i][c] = sk[c];
                 }
-                const T f = v[i][kk];
-                const T fi = f * inv;
+                const T fi = v[i][0] * inv;
 #pragma unroll
-                for (int c = 0; c < KB; ++c)
-                    if (c != kk) v[i][c] -= fi * sp[c];
-                v[i][kk] = -fi;
+                for (int c = 0; c < KB - 1; ++c) v[i][c] = v[i][c + 1] - fi * sp[c + 1];
+                v[i][KB - 1] = -fi;
             }
         }
     }
@@ -681,7 +685,6 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
     const size_t psmem = (size_t)b * KB * sizeof(T);
     auto kp = k_gj_panel<T, 512>;
     ensure_smem((const void*)kp, psmem);
-    const int rpt = (b + 511) / 512;
     constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
     // rank-kw update of the columns [cA, cB) outside [k0, k0 + kw)
     auto update = [&](int k0, int kw, int cA, int cB) {
@@ -705,9 +708,9 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
         const int KOi = (b - K0) < KO ? (b - K0) : KO;
         for (int k0 = K0; k0 < K0 + KOi; k0 += KB) {
             const int kbi = (K0 + KOi - k0) < KB ? (K0 + KOi - k0) : KB;
-            if (kbi == KB && rpt <= 2) {  // panel rows fit in registers (<= 2 per thread)
-                if (rpt == 1) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-                else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+            if (kbi == KB && b <= 1024) {  // panel rows in registers, one per thread
+                if (b <= 512) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+                else k_gj_panel_reg<T, 1024, 1, KB><<<count, 1024, 0, s>>>(mats, b, k0, ws_piv, info, amax);
             } else {
                 kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
             }

@@ -57,12 +57,15 @@ cudaError_t hodlr_omega(T* om, long long n, uint64_t seed, cudaStream_t s) {
 
 // ---------------------------------------------------------------- GEMM
 // Batched C_p = op(A_p) B_p, uniform M, N, K and leading dimensions; op(A) =
-// A (M x K, column-major) or A^T (A stored K x M).  SIMT, 64 x 32 tiles.
+// A (M x K, column-major) or A^T (A stored K x M).  SIMT, 64 x 32 tiles, k
+// steps of 32; the next step's operands are loaded into registers while the
+// current one is multiplied, so one memory latency is paid per step.
 template <class T, bool TA>
 __global__ void __launch_bounds__(256)
 k_gemm_gen(const T* const* __restrict__ Ap, const T* const* __restrict__ Bp, T* const* __restrict__ Cp, int M, int N,
            int K, int lda, int ldb, int ldc) {
-    constexpr int BM = 64, BN = 32, BK = 16, TM = 4, TN = 2, RY = BM / TM;
+    constexpr int BM = 64, BN = 32, BK = 32, TM = 4, TN = 2, RY = BM / TM;
+    constexpr int NA = BM * BK / 256, NB = BK * BN / 256;  // loads per thread per step
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     const T* A = Ap[blockIdx.y];
@@ -71,26 +74,45 @@ k_gemm_gen(const T* const* __restrict__ Ap, const T* const* __restrict__ Bp, T* 
     const int tiles_m = (M + BM - 1) / BM;
     const int row0 = (blockIdx.x % tiles_m) * BM, col0 = (blockIdx.x / tiles_m) * BN;
     const int tid = threadIdx.x, ty = tid % RY, tx = tid / RY;
+    T ra[NA], rb[NB];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int i = tid + u * 256;
+            int r, k;
+            if (TA) { k = i % BK; r = i / BK; } else { r = i % BM; k = i / BM; }
+            const int gr = row0 + r, gk = k0 + k;
+            ra[u] = (gr < M && gk < K) ? (TA ? A[gk + (size_t)gr * lda] : A[gr + (size_t)gk * lda]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int i = tid + u * 256;
+            const int k = i % BK, c = i / BK;
+            const int gk = k0 + k, gc = col0 + c;
+            rb[u] = (gk < K && gc < N) ? B[gk + (size_t)gc * ldb] : T(0);
+        }
+    };
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    load(0);
     for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int i = tid; i < BM * BK; i += 256) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+            const int i = tid + u * 256;
             int r, k;
             if (TA) { k = i % BK; r = i / BK; } else { r = i % BM; k = i / BM; }
-            const int gr = row0 + r, gk = k0 + k;
-            T v = T(0);
-            if (gr < M && gk < K) v = TA ? A[gk + (size_t)gr * lda] : A[gr + (size_t)gk * lda];
-            As[k][r] = v;
+            As[k][r] = ra[u];
         }
-        for (int i = tid; i < BK * BN; i += 256) {
-            const int k = i % BK, c = i / BK;
-            const int gk = k0 + k, gc = col0 + c;
-            Bs[k][c] = (gk < K && gc < N) ? B[gk + (size_t)gc * ldb] : T(0);
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int i = tid + u * 256;
+            Bs[i % BK][i / BK] = rb[u];
         }
         __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             T af[TM], bf[TN];
@@ -591,8 +613,8 @@ k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tas
 // spans b / CH items), the warps take the items round-robin and write each
 // item's partial t (rank x NR) to shared memory, and the partials of a node
 // are summed in item order.
-template <class T, int NR>
-__global__ void __launch_bounds__(256)
+template <class T, int NR, int NT>
+__global__ void __launch_bounds__(NT)
 k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms, const HTask* __restrict__ tasks,
          const HNode* __restrict__ nodes, const T* __restrict__ pool, int b, int L, int CH, int nrhs, int rkmax,
          T* __restrict__ tbuf) {
@@ -610,7 +632,8 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int per_level = b / CH, nitems = L * per_level;
     const int npb = (1 << (L + 1)) - 2;
-    for (int i = tid; i < npb; i += 256) {
+    constexpr int NW = NT / 32;
+    for (int i = tid; i < npb; i += NT) {
         const HTask tk = tasks[tb + i];
         const HNode hn = nodes[tk.node];
         s_toff[i] = tk.toff;
@@ -620,21 +643,21 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         __syncthreads();
-        for (int i0 = tid; i0 < b * NR; i0 += 8 * 256) {  // 8 loads in flight per thread
+        for (int i0 = tid; i0 < b * NR; i0 += 8 * NT) {  // 8 loads in flight per thread
             T xv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int i = i0 + u * 256, c = i % b, q = i / b;
+                const int i = i0 + u * NT, c = i % b, q = i / b;
                 xv[u] = (i < b * NR && q < nq) ? xval(P, term, c, q0 + q) : T(0);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int i = i0 + u * 256;
+                const int i = i0 + u * NT;
                 if (i < b * NR) xs[(i % b) * NR + i / b] = xv[u];
             }
         }
         __syncthreads();
-        for (int it = warp; it < nitems; it += 8) {
+        for (int it = warp; it < nitems; it += NW) {
             const int l = 1 + it / per_level, u = it % per_level;
             const int sz = b >> l, cpn = sz / CH;  // items per node
             const int ni = u / cpn, cc = u % cpn;
@@ -655,7 +678,7 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
 #pragma unroll
                 for (int q = 0; q < NR; ++q) acc[q] = T(0);
                 if (live) {
-#pragma unroll 4
+#pragma unroll 8
                     for (int j = j0 + g; j < j1; j += G) {
                         const T v = Vt[ii + (size_t)j * rk];
                         const T* xr = xs + (size_t)(c0 + j) * NR;
@@ -673,7 +696,7 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
         }
         __syncthreads();
         // node sums in item order: one warp per node, lanes over (rank index, column)
-        for (int nu = warp; nu < npb; nu += 8) {
+        for (int nu = warp; nu < npb; nu += NW) {
             const int rk = s_rk[nu];
             if (rk <= 0) continue;
             int l = 1;
@@ -884,7 +907,7 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
 // its inputs in its own slice of shared memory, streams the rows with 16-byte
 // loads, adds the column groups by shuffles and writes the tile.
 template <class T, int NR, int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_hrows_w(const HSweepProb<T>* __restrict__ probs, const HNode* __restrict__ nodes, const HTask* __restrict__ tasks,
           const T* __restrict__ tbuf, const T* __restrict__ pool, int b, int leaf, int L, int nrhs, int RT,
           int wmax) {
@@ -1006,17 +1029,28 @@ k_hrows_w(const HSweepProb<T>* __restrict__ probs, const HNode* __restrict__ nod
             for (int v = 0; v < V; ++v)
 #pragma unroll
                 for (int q = 0; q < NR; ++q) acc[v][q] += __shfl_xor_sync(0xffffffffu, acc[v][q], o);
+        // the tile's sums through this warp's slice (RT x NR <= wmax x NR), then
+        // every lane loads its cin values before storing its outputs
+        __syncwarp();
         if (g == 0)
 #pragma unroll
-            for (int q = 0; q < NR; ++q)
-                if (q < nq)
+            for (int v = 0; v < V; ++v)
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const size_t r = (size_t)row + v;
-                        T o = P.alpha * acc[v][q];
-                        if (P.cin) o += P.cin[r + (size_t)(q0 + q) * P.ldc];
-                        P.out[r + (size_t)(q0 + q) * P.ldo] = o;
-                    }
+                for (int q = 0; q < NR; ++q) xs[(rg * V + v) + q * RT] = acc[v][q];
+        __syncwarp();
+        constexpr int PER = 64 * NR / 32;  // outputs per lane at RT <= 64
+        T cv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int o = lane + u * 32, r = o % RT, q = o / RT;
+            cv[u] = (P.cin && o < RT * NR && q < nq) ? P.cin[R0 + r + (size_t)(q0 + q) * P.ldc] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int o = lane + u * 32, r = o % RT, q = o / RT;
+            if (o < RT * NR && q < nq) P.out[R0 + r + (size_t)(q0 + q) * P.ldo] = P.alpha * xs[o] + cv[u];
+        }
+        __syncwarp();
     }
 }
 
@@ -1055,8 +1089,10 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     const size_t sm = (size_t)std::max(b, 256 * V) * NR * sizeof(T);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
     // narrow tiles (the low reduction levels): one warp per tile
-    const bool by_warp = wmax > 0 && wmax <= 256 && L <= 31 && 32 % (RT / V) == 0;
-    const size_t smW = (size_t)8 * std::max(wmax, 1) * NR * sizeof(T);
+    // (wmax 0: only diagonal terms or copies)
+    const bool by_warp = wmax <= 256 && L <= 31 && 32 % (RT / V) == 0 && RT <= 64;
+    const int wslice = std::max(wmax, RT);  // the slice also holds the tile's RT x NR sums
+    const size_t smW = (size_t)8 * wslice * NR * sizeof(T);
     // few row tiles: split each tile's columns over CTAs so that every SM streams
     int nsplit = 1;
     const long long tiles = (long long)nprob * (b / RT);
@@ -1082,10 +1118,15 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
     {                                                                                                            \
         if (per_term) {                                                                                          \
-            if (nterms > 0) {                                                                                    \
-                ensure_smem((const void*)k_hnodes<T, NRV>, smT);                                               \
-                k_hnodes<T, NRV><<<nterms, 256, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH, nrhs,   \
-                                                          std::max(rkmax, 1), tbuf);                             \
+            if (nterms >= 152) {                                                                                 \
+                ensure_smem((const void*)k_hnodes<T, NRV, 256>, smT);                                          \
+                k_hnodes<T, NRV, 256><<<nterms, 256, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH,    \
+                                                               nrhs, std::max(rkmax, 1), tbuf);                  \
+                count_launches(1);                                                                               \
+            } else if (nterms > 0) { /* less than a wave: four times the warps per term */                      \
+                ensure_smem((const void*)k_hnodes<T, NRV, 1024>, smT);                                         \
+                k_hnodes<T, NRV, 1024><<<nterms, 1024, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH,  \
+                                                                 nrhs, std::max(rkmax, 1), tbuf);                \
                 count_launches(1);                                                                               \
             }                                                                                                    \
         } else if (na > 0) {                                                                                     \
@@ -1096,7 +1137,7 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
         if (by_warp) {                                                                                           \
             ensure_smem((const void*)k_hrows_w<T, NRV, V>, smW);                                               \
             k_hrows_w<T, NRV, V><<<dim3((b / RT + 7) / 8, nprob), 256, smW, s>>>(                              \
-                probs_all + prob_off, nodes, tasks, tbuf, pool, b, leaf, L, nrhs, RT, std::max(wmax, 1));        \
+                probs_all + prob_off, nodes, tasks, tbuf, pool, b, leaf, L, nrhs, RT, wslice);                   \
         } else {                                                                                                 \
             ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                  \
             k_hrows<T, NRV, V><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf,\
