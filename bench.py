@@ -351,9 +351,11 @@ def run_ours(args):
     sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
     if prec == "fp32tc":
         if peaks:
-            peak, src = peaks["bf16_tflops_sustained"] / 2.0, "of measured (bf16 sustained x 1/2, tf32 nominal ratio)"
+            peak, src = (peaks["bf16_tflops_sustained"] / 2.0 / 3.0,
+                         "of measured: bf16 sustained x 1/2 (tf32 nominal ratio) / 3 (three TF32 MMAs per "
+                         "FP32-accurate product term)")
         else:
-            peak, src = 1700.0 / 2.0, "of fallback"
+            peak, src = 1700.0 / 2.0 / 3.0, "of fallback (x 1/2 tf32, / 3 split terms)"
         bound = "tensor"
     elif prec == "fp32":
         peak, src = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"

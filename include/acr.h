@@ -86,7 +86,9 @@ typedef struct {
     double ir_tol;      /* refinement target ||f - M x||_2 / ||f||_2 per column
                            (default 1e-8) */
     int ir_max_iter;    /* cap on preconditioner solves per acr_solve (default 20) */
-    void *stream;       /* cudaStream_t to run on; NULL: a library stream */
+    void *stream;       /* cudaStream_t to run on (it must outlive the handle:
+                           the factorization's memory is allocated and freed
+                           in stream order on it); NULL: a library stream */
     int refine;         /* enum acr_refine, default ACR_REFINE_FGMRES */
 } acr_opts;
 
@@ -132,7 +134,11 @@ int acr_solve(acr_handle h, double *B, int nrhs);
  * (iters_out, may be NULL; 0 when no refinement ran). */
 int acr_solve_ex(acr_handle h, double *B, int nrhs, double *resid_out, int *iters_out);
 
-/* Release everything the handle holds.  NULL is a no-op. */
+/* Release everything the handle holds.  NULL is a no-op.  Device memory goes
+ * back, in stream order, to the device's default stream-ordered pool; the
+ * library raises that pool's release threshold to 64 GiB (once per device,
+ * never lowering it), so freed memory stays mapped in this process for the
+ * next factorization instead of being returned to the driver. */
 void acr_free(acr_handle h);
 
 typedef struct {

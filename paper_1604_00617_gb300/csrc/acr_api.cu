@@ -31,6 +31,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -109,12 +110,6 @@ struct DevBuf {
         if (bytes == 0) bytes = 16;
         return cudaMallocAsync(&p, bytes, st);
     }
-    cudaError_t alloc_sync(size_t bytes) {
-        release();
-        async = false;
-        if (bytes == 0) bytes = 16;
-        return cudaMalloc(&p, bytes);
-    }
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
@@ -149,8 +144,14 @@ struct acr_ctx {
     std::mutex mu;
     acr_stats_t st{};
     ~acr_ctx() {
+        // stream-ordered frees, all queued before the stream may be destroyed
         arena.release();
         op.release();
+        hpool.release();
+        hnodes.release();
+        hblks.release();
+        hdiag.release();
+        if (stream) cudaStreamSynchronize(stream);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
     size_t bb() const { return (size_t)b * b; }
@@ -422,9 +423,9 @@ int compress_factor(acr_ctx* h) {
             }
     }
     const size_t pool_bytes = (size_t)off * sizeof(T);
-    CK(h->hpool.alloc_sync(pool_bytes));
-    CK(h->hnodes.alloc_sync(std::max<size_t>(1, nodes.size()) * sizeof(HNode)));
-    CK(h->hblks.alloc_sync((size_t)NB * sizeof(HBlk)));
+    CK(h->hpool.alloc(pool_bytes, h->stream));
+    CK(h->hnodes.alloc(std::max<size_t>(1, nodes.size()) * sizeof(HNode), h->stream));
+    CK(h->hblks.alloc((size_t)NB * sizeof(HBlk), h->stream));
     if (!nodes.empty())
         CK(cudaMemcpyAsync(h->hnodes.p, nodes.data(), nodes.size() * sizeof(HNode), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->hblks.p, hb.data(), (size_t)NB * sizeof(HBlk), cudaMemcpyHostToDevice, s));
@@ -483,7 +484,7 @@ int compress_factor(acr_ctx* h) {
         const size_t src4[4] = {L0.off_xa, L0.off_xc, L0.off_ak, L0.off_ck};
         size_t tot = 0;
         for (int i = 0; i < 4; ++i) { h->hd_off[i] = tot; tot += n4[i]; }
-        CK(h->hdiag.alloc_sync(std::max<size_t>(tot, 1) * sizeof(T)));
+        CK(h->hdiag.alloc(std::max<size_t>(tot, 1) * sizeof(T), h->stream));
         for (int i = 0; i < 4; ++i)
             CK(cudaMemcpyAsync(h->hdiag.as<T>() + h->hd_off[i], h->P<T>(src4[i]), n4[i] * sizeof(T),
                                cudaMemcpyDeviceToDevice, s));
@@ -534,7 +535,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     // ---- FP64 operator copy (residual of the refinement) -----------------
     if (banded) {
         const size_t N = (size_t)n * b;
-        CK(h->op.alloc_sync(5 * N * 8));
+        CK(h->op.alloc(5 * N * 8, h->stream));
         double* o = h->op.as<double>();
         // Dl, Dd, Du de-interleaved from [sub, diag, super] per block
         for (int d = 0; d < 3; ++d)
@@ -548,7 +549,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         CK(cudaMemsetAsync(o + 4 * N + (N - b), 0, b * 8, s));
         h->st.operator_bytes = 5 * N * 8;
     } else {
-        CK(h->op.alloc_sync(3 * (size_t)n * bb * 8));
+        CK(h->op.alloc(3 * (size_t)n * bb * 8, h->stream));
         double* o = h->op.as<double>();
         if (n > 1) {
             CK(cudaMemcpyAsync(o, dA, (size_t)n * bb * 8, cudaMemcpyDeviceToDevice, s));
@@ -582,7 +583,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
 
     // ---- persistent arena -------------------------------------------------
     const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev, b0);
-    CK(h->arena.alloc_sync(arena_bytes));
+    CK(h->arena.alloc(arena_bytes, h->stream));
     h->st.factor_bytes = arena_bytes;
     const int T_ = h->levels() - 1;
 
@@ -1579,6 +1580,31 @@ int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts* o, size_t*
     return ACR_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Freed stream-ordered memory stays in the device's default pool (up to
+// 64 GiB, or the process's own higher setting), so that repeated
+// factorizations and the per-call temporaries reuse mapped memory instead of
+// mapping it again on every call.  A property of this process's pool only.
+void keep_pool_memory(int dev) {
+    static std::mutex mu;
+    static std::set<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(dev)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t cur = 0, want = 64ull << 30;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < want)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+    }
+    cudaGetLastError();
+    done.insert(dev);
+}
+}  // namespace
+
+extern "C" {
+
 int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const double* C, double tol,
                   const acr_opts* o, acr_handle* out) {
     if (!out) return fail(ACR_ERR_INVALID_ARG, "out is NULL");
@@ -1597,6 +1623,7 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     if (!h) return fail(ACR_ERR_OOM, "host allocation failed");
     h->n = nblk; h->b = blksz; h->prec = op.precision; h->in_kind = op.input_kind; h->tol = tol; h->opts = op;
     cudaGetDevice(&h->dev);
+    keep_pool_memory(h->dev);
     if (op.stream) {
         h->stream = static_cast<cudaStream_t>(op.stream);
     } else {
