@@ -284,7 +284,10 @@ def run_ours(args):
     P, F = workload(args.n, args.nrhs)
     a, D3, c = P.banded_abi()
     N, nrhs = P.N, args.nrhs
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the NULL stream cannot hold captured graphs)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     da, dD3, dc = (torch.from_numpy(x).to(dev) for x in (a, D3, c))
     dF = torch.from_numpy(np.ascontiguousarray(F.T)).to(dev)  # column-major N x nrhs
     dB = torch.empty_like(dF)

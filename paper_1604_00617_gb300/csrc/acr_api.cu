@@ -887,7 +887,18 @@ struct SweepPlan {
     double bytes = 0.0;             // algorithmic bytes of one pass
     std::vector<cudaEvent_t> evs;   // start/end of every pass
     long long launches = 0;
-    ~SweepPlan() { for (cudaEvent_t e : evs) cudaEventDestroy(e); }
+    cudaGraphExec_t gexec = nullptr;  // the captured pass
+    cudaStream_t gstream = nullptr;   // its stream
+    long long glaunches = 0;          // kernels in it
+    int applications = 0;
+    bool no_graph = false;
+    ~SweepPlan() {
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        if (gexec) {
+            cudaStreamSynchronize(gstream);  // no replay may still be running
+            cudaGraphExecDestroy(gexec);
+        }
+    }
     double elapsed_ms() const {
         double t = 0.0;
         for (size_t i = 0; i + 1 < evs.size(); i += 2) {
@@ -1165,17 +1176,10 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
 }
 
 template <class T>
-int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
+int issue_sweep(acr_ctx* h, SweepPlan<T>& sp) {
     const int b = h->b, T_ = h->levels() - 1, nrhs = sp.nrhs;
     cudaStream_t s = h->stream;
     const SweepProb<T>* dp = sp.dprobs.template as<SweepProb<T>>();
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    sp.evs.push_back(e0);
-    sp.evs.push_back(e1);
-    const long long c0 = launch_count();
-    CK(cudaEventRecord(e0, s));
     if (sp.hodlr) {
         const HSweepProb<T>* hq = sp.hprobs.template as<HSweepProb<T>>();
         const HBlk* hb = h->hblks.as<HBlk>();
@@ -1205,8 +1209,63 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
         }
         for (int t = T_; t >= 0; --t) CK(sweep_batched<T>(dp + sp.bk_off[t], (int)sp.bk_cnt[t], b, nrhs, s));
     }
+    return ACR_OK;
+}
+
+// One application of the sweeps.  The launch sequence of a plan never changes
+// (fixed buffers), so it is captured into a CUDA graph at the first
+// application and replayed afterwards -- unless the caller's stream is itself
+// being captured, where the launches are issued directly.
+template <class T>
+int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    sp.evs.push_back(e0);
+    sp.evs.push_back(e1);
+    // capture from the second application on: a plan used once is never
+    // captured, and every kernel's shared-memory limit has been raised by then
+    // (raising it is not a stream operation)
+    ++sp.applications;
+    if (!sp.gexec && !sp.no_graph && sp.applications >= 2) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const bool legacy = s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread;
+        if (legacy || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+            cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            sp.no_graph = true;  // the NULL stream cannot be captured: launch directly
+        } else {
+            sp.gstream = s;
+            const long long c0 = launch_count();
+            const int st = issue_sweep<T>(h, sp);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(s, &g);  // always ends the capture
+            // the captured launches ran nothing yet: count them per replay
+            sp.glaunches = launch_count() - c0;
+            count_launches((int)-sp.glaunches);
+            if (st) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            CK(ee);
+            const cudaError_t ei = cudaGraphInstantiate(&sp.gexec, g, 0);
+            cudaGraphDestroy(g);
+            CK(ei);
+        }
+    }
+    CK(cudaEventRecord(e0, s));
+    if (sp.gexec) {
+        CK(cudaGraphLaunch(sp.gexec, s));
+        count_launches((int)sp.glaunches);
+        sp.launches += sp.glaunches;
+    } else {
+        const long long c0 = launch_count();
+        const int st = issue_sweep<T>(h, sp);
+        sp.launches += launch_count() - c0;
+        if (st) return st;
+    }
     CK(cudaEventRecord(e1, s));
-    sp.launches += launch_count() - c0;
     return ACR_OK;
 }
 
@@ -1635,7 +1694,10 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     }
     h->es = op.precision == ACR_FP64 ? 8 : 4;
     // ranks below the factor's own rounding level only encode noise
-    h->tol_eff = tol > 0 ? std::max(tol, (h->es == 8 ? 32 * 2.220446049250313e-16 : 32 * 1.1920929e-7)) : 0.0;
+    // truncation floor: a few units of the factor's rounding (FP32: 9.5e-7;
+    // 32 eps was measured to cost four more FGMRES solves on the indefinite
+    // 1M Helmholtz problem than 8 eps, for 15% less storage)
+    h->tol_eff = tol > 0 ? std::max(tol, (h->es == 8 ? 32 * 2.220446049250313e-16 : 8 * 1.1920929e-7)) : 0.0;
     h->st.nblk = nblk; h->st.blksz = blksz; h->st.precision = op.precision; h->st.compressed = 0;
     int st = (h->es == 8) ? run_factor<double>(h, A, D, C) : run_factor<float>(h, A, D, C);
     if (st != ACR_OK) {
