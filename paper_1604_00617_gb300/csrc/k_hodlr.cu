@@ -417,6 +417,161 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
     }
 }
 
+// Small nodes (s <= 128 rows, k <= 16 sketch columns): one warp per node, the
+// same steps as k_node_svd -- Householder QR of Y, one-sided Jacobi on the
+// columns of R (lane c holds column c), U = Q [W; 0] with W the normalised
+// rotated columns, singular values in decreasing order (ties by index) --
+// with the node's panels in the warp's own slice of shared memory, so that
+// no step waits for the other warps of the CTA.
+template <class T>
+__global__ void __launch_bounds__(128)
+k_node_svd_w(const T* __restrict__ Yall, T* __restrict__ Uall, T* __restrict__ sig_all, int nnodes, int s, int k) {
+    constexpr int KK = 16;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t node = (size_t)blockIdx.x * 4 + warp;
+    if (node >= (size_t)nnodes) return;
+    const size_t per = 2 * (size_t)s * k + (size_t)k * k + k;
+    T* Y = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per;  // s x k: the panel, then the reflectors
+    T* Z = Y + (size_t)s * k;                                     // s x k: [W; 0], then U (unsorted)
+    T* R = Z + (size_t)s * k;                                     // k x k
+    T* tau = R + (size_t)k * k;                                   // k
+    const T* Yg = Yall + node * (size_t)s * k;
+    for (int i0 = lane; i0 < s * k; i0 += 8 * 32) {  // 8 loads in flight per lane
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (i0 + u * 32 < s * k) ? Yg[i0 + u * 32] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + u * 32 < s * k) Y[i0 + u * 32] = v[u];
+    }
+    __syncwarp();
+    // ---- Householder QR (H = I - tau v v^T, v[j] = 1) ----
+    for (int j = 0; j < k; ++j) {
+        T* col = Y + (size_t)j * s;
+        T part = T(0);
+        for (int r = j + 1 + lane; r < s; r += 32) part += col[r] * col[r];
+        const T xn2 = warp_sum(part);
+        const T alpha = col[j];
+        T tj, rjj, scl;
+        if (xn2 == T(0)) {
+            tj = T(0); rjj = alpha; scl = T(0);
+        } else {
+            T beta = sqrt(alpha * alpha + xn2);
+            if (alpha > T(0)) beta = -beta;
+            tj = (beta - alpha) / beta; rjj = beta; scl = T(1) / (alpha - beta);
+        }
+        __syncwarp();
+        if (xn2 != T(0))
+            for (int r = j + 1 + lane; r < s; r += 32) col[r] *= scl;
+        if (lane == 0) { tau[j] = tj; R[j + j * k] = rjj; col[j] = T(1); }
+        __syncwarp();
+        for (int c = j + 1; c < k; ++c) {
+            T* cc = Y + (size_t)c * s;
+            T d = T(0);
+            for (int r = j + lane; r < s; r += 32) d += col[r] * cc[r];
+            d = warp_sum(d) * tj;
+            for (int r = j + lane; r < s; r += 32) cc[r] -= d * col[r];
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < k * k; i += 32) {
+        const int r = i % k, c = i / k;
+        if (r < c) R[i] = Y[(size_t)c * s + r];
+        else if (r > c) R[i] = T(0);
+    }
+    __syncwarp();
+    // ---- one-sided Jacobi on R's columns, lane c holds column c ----
+    const T eps = sizeof(T) == 8 ? T(4e-15) : T(4e-7);
+    T cl[KK];
+#pragma unroll
+    for (int r = 0; r < KK; ++r) cl[r] = (lane < k && r < k) ? R[r + lane * k] : T(0);
+    T nrm = T(0);
+#pragma unroll
+    for (int r = 0; r < KK; ++r) nrm = fma(cl[r], cl[r], nrm);
+    const T negl = warp_sum(nrm) * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
+    const int km1 = k - 1;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        bool rot = false;
+        for (int rnd = 0; rnd < km1; ++rnd) {
+            int partner = lane;
+            bool is_a = false;
+            if (lane < k) {
+                if (lane == km1) { partner = rnd; is_a = true; }
+                else if (lane == rnd) { partner = km1; }
+                else {
+                    partner = ((2 * rnd - lane) % km1 + km1) % km1;
+                    const int d = ((lane - rnd) % km1 + km1) % km1;
+                    is_a = d >= 1 && d <= k / 2 - 1;
+                }
+            }
+            T pc[KK];
+#pragma unroll
+            for (int r = 0; r < KK; ++r) pc[r] = __shfl_sync(FULL, cl[r], partner);
+            const T pn = __shfl_sync(FULL, nrm, partner);
+            T ga = T(0);
+#pragma unroll
+            for (int r = 0; r < KK; ++r) ga = fma(cl[r], pc[r], ga);
+            const T al = is_a ? nrm : pn, be = is_a ? pn : nrm;
+            if (partner != lane && al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                const T zeta = (be - al) / (T(2) * ga);
+                const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+                T n2 = T(0);
+                if (is_a) {
+#pragma unroll
+                    for (int r = 0; r < KK; ++r) { cl[r] = c * cl[r] - sn * pc[r]; n2 = fma(cl[r], cl[r], n2); }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < KK; ++r) { cl[r] = sn * pc[r] + c * cl[r]; n2 = fma(cl[r], cl[r], n2); }
+                }
+                nrm = n2;
+                rot = true;
+            }
+        }
+        if (!__any_sync(FULL, rot)) break;
+    }
+    // ---- singular values, their order, W = R J / sigma ----
+    const T sv = sqrt(nrm);
+    const T key = isnan(sv) ? T(-1) : sv;
+    int pos = 0;
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+        const T kj = __shfl_sync(FULL, key, j);
+        if (j < k) pos += (kj > key) || (kj == key && j < lane);
+    }
+    for (int i = lane; i < s * k; i += 32) Z[i] = T(0);
+    __syncwarp();
+    if (lane < k) {
+#pragma unroll
+        for (int r = 0; r < KK; ++r)
+            if (r < k) Z[(size_t)lane * s + r] = sv > T(0) ? cl[r] / sv : T(0);
+    }
+    __syncwarp();
+    // ---- U = Q [W; 0], reflectors in reverse order ----
+    for (int j = k - 1; j >= 0; --j) {
+        const T tj = tau[j];
+        if (tj == T(0)) continue;
+        const T* v = Y + (size_t)j * s;
+        for (int c = 0; c < k; ++c) {
+            T* zc = Z + (size_t)c * s;
+            T d = T(0);
+            for (int r = j + lane; r < s; r += 32) d += v[r] * zc[r];
+            d = warp_sum(d) * tj;
+            for (int r = j + lane; r < s; r += 32) zc[r] -= d * v[r];
+        }
+        __syncwarp();
+    }
+    T* Ug = Uall + node * (size_t)s * k;
+    T* sg = sig_all + node * k;
+    for (int c = 0; c < k; ++c) {
+        const int p = __shfl_sync(FULL, pos, c);
+        for (int r = lane; r < s; r += 32) Ug[r + (size_t)p * s] = Z[r + (size_t)c * s];
+    }
+    if (lane < k) sg[pos] = sv;
+}
+
 template <class T>
 size_t node_svd_smem(int s, int k, int kz) {
     return ((size_t)s * k + (size_t)k * k + 2 * (size_t)k + (size_t)s * kz) * sizeof(T) + (size_t)k * sizeof(int);
@@ -432,6 +587,13 @@ int node_svd_kz(int s, int k) {  // widest work panel that fits in 200 KB
 template <class T>
 cudaError_t node_svd(const T* Y, T* U, T* sig, int nnodes, int s, int k, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
+    if (s <= 128 && k <= 16) {  // one warp per node, four per CTA
+        const size_t sm = 4 * (2 * (size_t)s * k + (size_t)k * k + k) * sizeof(T);
+        ensure_smem((const void*)k_node_svd_w<T>, sm);
+        k_node_svd_w<T><<<(nnodes + 3) / 4, 128, sm, st>>>(Y, U, sig, nnodes, s, k);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int kz = node_svd_kz<T>(s, k);
     if (kz == 0) return cudaErrorInvalidValue;
     const size_t sm = node_svd_smem<T>(s, k, kz);
