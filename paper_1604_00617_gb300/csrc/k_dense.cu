@@ -1470,6 +1470,47 @@ __global__ void k_multi_dot_partial(const double* __restrict__ V, const double* 
     }
 }
 
+// grid (chunks, nrhs): one CTA per chunk of DW = 16 x 256 rows holds its
+// rows of w in registers and forms all nvec partial products from them
+// (w read once, 16 independent loads of V in flight per thread);
+// ws[(i * nrhs + q) * chunks + c] as k_multi_dot_partial.
+constexpr int DW = 16;
+__global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ V, int nvec,
+                                                     const double* __restrict__ w, long long N, int nrhs,
+                                                     double* __restrict__ ws) {
+    __shared__ double red[8];
+    const int q = blockIdx.y, chunks = gridDim.x, tid = threadIdx.x;
+    const long long lo = (long long)blockIdx.x * DW * 256;
+    const double* wq = w + (long long)q * N;
+    double wr[DW];
+#pragma unroll
+    for (int u = 0; u < DW; ++u) {
+        const long long r = lo + tid + u * 256;
+        wr[u] = r < N ? wq[r] : 0.0;
+    }
+    for (int i = 0; i < nvec; ++i) {
+        const double* vq = V + ((long long)i * nrhs + q) * N;
+        double v[DW];
+#pragma unroll
+        for (int u = 0; u < DW; ++u) {
+            const long long r = lo + tid + u * 256;
+            v[u] = r < N ? vq[r] : 0.0;
+        }
+        double sum = 0.0;
+#pragma unroll
+        for (int u = 0; u < DW; ++u) sum = fma(v[u], wr[u], sum);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((tid & 31) == 0) red[tid >> 5] = sum;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < 8; ++k) t += red[k];
+            ws[((long long)i * nrhs + q) * chunks + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
 static int dot_chunks(long long N) {
     int chunks = 256;
     if (N < 256LL * 1024) chunks = (int)((N + 1023) / 1024);
@@ -1479,6 +1520,15 @@ static int dot_chunks(long long N) {
 cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws, double* out,
                       cudaStream_t s) {
     if (nvec <= 0 || nrhs <= 0) return cudaSuccess;
+    // the workspace holds 1024 partials per product
+    const long long cw = (N + (long long)DW * 256 - 1) / ((long long)DW * 256);
+    if (cw <= 1024) {
+        k_multi_dot_w<<<dim3((int)cw, nrhs), 256, 0, s>>>(V, nvec, w, N, nrhs, ws);
+        count_launches(1);
+        k_sumsq_final<<<nvec * nrhs, 256, 0, s>>>(ws, (int)cw, out);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const int chunks = dot_chunks(N);
     k_multi_dot_partial<<<dim3(chunks, nrhs, nvec), 256, 0, s>>>(V, w, N, nrhs, ws);
     count_launches(1);

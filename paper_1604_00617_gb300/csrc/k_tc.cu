@@ -13,11 +13,12 @@
 //               column-major layout) and B tile (32 k x 128 cols, loaded with
 //               the 128-byte swizzle = the K-major operand layout);
 //   warp 1      allocates 128 TMEM columns and issues the MMAs (one thread);
-//   warps 2..5  split each stage into hi/lo operand tiles (A transposed into
+//   warps 2..9  split each stage into hi/lo operand tiles (A transposed into
 //               the K-major swizzled layout), then run the epilogue
 //               (tcgen05.ld, alpha/beta, coalesced column-major stores).
-// Two pipeline stages, mbarrier handshakes; every wait is bounded and a
-// timeout sets *err instead of hanging.
+// A 3-stage ring of raw copies feeds a 2-stage ring of split operands, with
+// mbarrier handshakes; every wait is bounded and a timeout sets *err instead
+// of hanging.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -42,7 +43,7 @@ constexpr int RAW = 3, CONV = 2;
 constexpr int RAW_BYTES = 2 * TILE_BYTES, CONV_BYTES = 4 * TILE_BYTES;
 constexpr int SMEM_BYTES = RAW * RAW_BYTES + CONV * CONV_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;  // producer, MMA issuer, 8 converter / epilogue warps
 constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -160,10 +161,10 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
     if (threadIdx.x == 0) {
         for (int i = 0; i < RAW; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&raw_free[i], 4);
+            mbar_init(&raw_free[i], 8);
         }
         for (int i = 0; i < CONV; ++i) {
-            mbar_init(&conv_full[i], 4);
+            mbar_init(&conv_full[i], 8);
             mbar_init(&conv_free[i], 1);
         }
         mbar_init(accb, 1);
@@ -217,8 +218,9 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
             mma_commit(accb);
         }
     } else {
-        // ---- converters (warps 2..5, 128 threads) --------------------------
+        // ---- converters (warps 2..9, 256 threads: two per scheduler) --------
         const int t = threadIdx.x - 64;
+        const int am = t & (BM - 1), ah = t >> 7;  // A: row am, k chunks [4 ah, 4 ah + 4)
         for (int it = 0; it < niter; ++it) {
             const int r = it % RAW, c = it % CONV;
             if (!mbar_wait(&full[r], (uint32_t)((it / RAW) & 1))) { s_fail = 1; break; }
@@ -231,23 +233,24 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
             unsigned char* alo = cv + TILE_BYTES;
             float4* bhi = reinterpret_cast<float4*>(cv + 2 * TILE_BYTES);
             float4* blo = reinterpret_cast<float4*>(cv + 3 * TILE_BYTES);
-            // A: row m = t, 8 chunks of 4 k -> K-major swizzled hi / lo
+            // A: row am, 4 chunks of 4 k -> K-major swizzled hi / lo
 #pragma unroll
-            for (int q = 0; q < BK / 4; ++q) {
+            for (int qq = 0; qq < BK / 8; ++qq) {
+                const int q = ah * (BK / 8) + qq;
                 float4 h, l;
                 float x;
-                x = araw[(4 * q + 0) * BM + t]; h.x = tf32_hi(x); l.x = tf32_rn(x - h.x);
-                x = araw[(4 * q + 1) * BM + t]; h.y = tf32_hi(x); l.y = tf32_rn(x - h.y);
-                x = araw[(4 * q + 2) * BM + t]; h.z = tf32_hi(x); l.z = tf32_rn(x - h.z);
-                x = araw[(4 * q + 3) * BM + t]; h.w = tf32_hi(x); l.w = tf32_rn(x - h.w);
-                const uint32_t o = sw128_off(t, 4 * q);
+                x = araw[(4 * q + 0) * BM + am]; h.x = tf32_hi(x); l.x = tf32_rn(x - h.x);
+                x = araw[(4 * q + 1) * BM + am]; h.y = tf32_hi(x); l.y = tf32_rn(x - h.y);
+                x = araw[(4 * q + 2) * BM + am]; h.z = tf32_hi(x); l.z = tf32_rn(x - h.z);
+                x = araw[(4 * q + 3) * BM + am]; h.w = tf32_hi(x); l.w = tf32_rn(x - h.w);
+                const uint32_t o = sw128_off(am, 4 * q);
                 *reinterpret_cast<float4*>(ahi + o) = h;
                 *reinterpret_cast<float4*>(alo + o) = l;
             }
             // B: already in the K-major swizzled layout; split element-wise
 #pragma unroll
-            for (int j = 0; j < TILE_BYTES / 16 / 128; ++j) {
-                const int i = t + j * 128;
+            for (int j = 0; j < TILE_BYTES / 16 / 256; ++j) {
+                const int i = t + j * 256;
                 const float4 v = braw[i];
                 float4 h, l;
                 h.x = tf32_hi(v.x); l.x = tf32_rn(v.x - h.x);
@@ -270,8 +273,9 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp & 3;  // TMEM lane quarter this warp may read
         const int row = m0 + q * 32 + lane;
+        const int half = (warp - 2) >> 2;  // two warps per quarter: columns [64 half, 64 half + 64)
 #pragma unroll 1
-        for (int cj = 0; cj < BN / 32; ++cj) {
+        for (int cj = half * (BN / 64); cj < (half + 1) * (BN / 64); ++cj) {
             uint32_t r[32];
             const uint32_t taddr = tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(cj * 32);
             asm volatile(
