@@ -144,3 +144,23 @@ def test_tiny_tol_matches_dense(lib):
         lib.acr_free(hd)
         lib.acr_free(hc)
     assert np.linalg.norm(Xc - Xd) / np.linalg.norm(Xd) <= 1e-11
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-8])
+def test_graph_replay_matches_direct_launches(lib, tol):
+    """The solve sweeps are replayed as a captured CUDA graph on a library
+    stream; on the legacy NULL stream (handle value 1), which cannot be
+    captured, the same launches are issued directly.  Both give the same
+    bits."""
+    P = syn.make_config(3, 128)
+    F = syn.rhs_uniform(P.N, 3, 2003)
+    X = []
+    for stream in (None, 1):
+        h = factor(lib, P, tol, prec=lib.ACR_FP32TC_IR, leaf=32, ir_max_iter=60, stream=stream)
+        try:
+            x, res, it = solve(lib, h, F)
+        finally:
+            lib.acr_free(h)
+        assert (res <= 1e-8).all() and it > 2  # several preconditioner solves: the graph is replayed
+        X.append(x)
+    assert np.array_equal(X[0], X[1])
