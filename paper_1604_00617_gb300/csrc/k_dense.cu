@@ -560,7 +560,7 @@ __global__ void k_gj_gather_tc(T* __restrict__ mats, int b, int k0, int kb, cons
     int* perm = reinterpret_cast<int*>(sh_raw);  // b
     int* slot = perm + b;                        // b
     int* list = slot + b;                        // kb
-    T* vals = reinterpret_cast<T*>(sh_raw + (((size_t)(2 * b + kb) * sizeof(int) + 15) & ~(size_t)15));  // 2kb x 32
+    T* vals = reinterpret_cast<T*>(sh_raw + (((size_t)(2 * b + kb) * sizeof(int) + 15) & ~(size_t)15));  // 2kb x 33
     __shared__ int s_cnt;
     T* G = mats + (size_t)blockIdx.y * b * b;
     const int* piv = pivs + (size_t)blockIdx.y * b;
@@ -583,21 +583,80 @@ __global__ void k_gj_gather_tc(T* __restrict__ mats, int b, int k0, int kb, cons
     __syncthreads();
     const int ns = kb + s_cnt;
     const int c0 = blockIdx.x * 32;
+    // consecutive threads take consecutive slots of one column: the pivot rows
+    // of a panel are mostly consecutive rows, so reads and writes coalesce
     for (int i = threadIdx.x; i < ns * 32; i += blockDim.x) {
-        const int sl = i >> 5, j = i & 31, c = c0 + j;
+        const int sl = i % ns, j = i / ns, c = c0 + j;
         const int r = sl < kb ? k0 + sl : list[sl - kb];
-        vals[i] = c < b ? G[perm[r] + (size_t)c * b] : T(0);
+        vals[sl * 33 + j] = c < b ? G[perm[r] + (size_t)c * b] : T(0);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kb * 32; i += blockDim.x) {
         const int sl = i % kb, j = i / kb, c = c0 + j;
-        if (c < b) st[(size_t)c * kb + sl] = vals[sl * 32 + j];
+        if (c < b) st[(size_t)c * kb + sl] = vals[sl * 33 + j];
     }
     for (int i = threadIdx.x; i < ns * 32; i += blockDim.x) {
-        const int sl = i >> 5, j = i & 31, c = c0 + j;
+        const int sl = i % ns, j = i / ns, c = c0 + j;
         if (c >= b || (c >= k0 && c < k0 + kb)) continue;
         const int r = sl < kb ? k0 + sl : list[sl - kb];
-        G[r + (size_t)c * b] = sl < kb ? T(0) : vals[i];
+        G[r + (size_t)c * b] = sl < kb ? T(0) : vals[sl * 33 + j];
+    }
+}
+
+// Column interchanges of the blocked path as one permutation: CTA z composes
+// block z's interchanges (applied in reverse pivot order, in shared memory)
+// into src[c] = the column that ends at position c.
+__global__ void k_gj_perm(const int* __restrict__ pivs, int b, int* __restrict__ srcs) {
+    extern __shared__ int sh_p[];
+    int* piv = sh_p;      // b
+    int* src = sh_p + b;  // b
+    const int z = blockIdx.x;
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+        piv[c] = pivs[(size_t)z * b + c];
+        src[c] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = b - 1; k >= 0; --k) {
+            const int p = piv[k];
+            if (p != k) {
+                const int t = src[k];
+                src[k] = src[p];
+                src[p] = t;
+            }
+        }
+    __syncthreads();
+    for (int c = threadIdx.x; c < b; c += blockDim.x) srcs[(size_t)z * b + c] = src[c];
+}
+
+// Apply it: a tile of UR rows x all b columns through shared memory (each
+// element read once and written once, UR consecutive rows per column).
+constexpr int UR = 16;
+template <class T>
+__global__ void k_gj_permute(T* __restrict__ mats, int b, const int* __restrict__ srcs) {
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    T* tile = reinterpret_cast<T*>(sh_raw);  // [b][UR]
+    T* G = mats + (size_t)blockIdx.y * b * b;
+    const int* src = srcs + (size_t)blockIdx.y * b;
+    const int r0 = blockIdx.x * UR;
+    const int nr = min(UR, b - r0);
+    for (int i0 = threadIdx.x; i0 < UR * b; i0 += 8 * blockDim.x) {  // 8 loads in flight per thread
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x, r = i % UR, c = i / UR;
+            v[u] = (i < UR * b && r < nr) ? G[(r0 + r) + (size_t)c * b] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < UR * b) tile[(i / UR) * UR + i % UR] = v[u];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < UR * b; i += blockDim.x) {
+        const int r = i % UR, c = i / UR;
+        if (r < nr) G[(r0 + r) + (size_t)c * b] = tile[src[c] * UR + r];
     }
 }
 
@@ -721,7 +780,7 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
         if constexpr (sizeof(T) == 4) {
             if (tco) {
                 const size_t gsm = (((size_t)(2 * b + KOi) * sizeof(int) + 15) & ~(size_t)15) +
-                                   (size_t)2 * KOi * 32 * sizeof(T);
+                                   (size_t)2 * KOi * 33 * sizeof(T);
                 ensure_smem((const void*)k_gj_gather_tc<T>, gsm);
                 k_gj_gather_tc<T><<<dim3((b + 31) / 32, count), 256, gsm, s>>>(mats, b, K0, KOi, ws_piv, tco->stT);
                 count_launches(1);
@@ -733,6 +792,17 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
             }
         }
         update(K0, KOi, 0, b);
+    }
+    const size_t usm = (size_t)UR * b * sizeof(T);
+    if (usm <= 160 * 1024 && 2 * (size_t)b * sizeof(int) <= 160 * 1024) {
+        // the slot map is free by now: it holds the composed permutation
+        ensure_smem((const void*)k_gj_perm, 2 * (size_t)b * sizeof(int));
+        k_gj_perm<<<count, 256, 2 * (size_t)b * sizeof(int), s>>>(ws_piv, b, slotmap);
+        count_launches(1);
+        ensure_smem((const void*)k_gj_permute<T>, usm);
+        k_gj_permute<T><<<dim3((b + UR - 1) / UR, count), 256, usm, s>>>(mats, b, slotmap);
+        count_launches(1);
+        return cudaGetLastError();
     }
     dim3 gu((b + 255) / 256, count);
     k_gj_unscramble<T><<<gu, 256, b * sizeof(int), s>>>(mats, b, ws_piv);

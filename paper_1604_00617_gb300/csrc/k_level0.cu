@@ -13,42 +13,52 @@
 
 namespace acr {
 
-// One thread per row r of D_j^-1.  The LU factors (l_k, u_k) of the
-// tridiagonal are recomputed per CTA in shared memory (b sequential steps).
+// One CTA per eliminated block (up to 512 threads), thread t handling rows
+// t, t + blockDim, ... of D_j^-1.  The three diagonals are staged
+// in shared memory with coalesced loads; thread 0 then runs the LU recurrence
+// (b sequential FP64 steps, all operands in shared memory).
 // Row r of X = T^-1 solves T^T y = e_r, i.e. U^T z = e_r (forward, z_c = 0
 // for c < r) then L^T y = z (backward).  z is written to X in the first pass
 // and overwritten by y in the second; both passes are coalesced across rows.
 template <class T>
-__global__ void k_tridiag_inv(const double* __restrict__ Dband, int n, int b, T* __restrict__ dinv,
-                              int* __restrict__ info) {
+__global__ void __launch_bounds__(512) k_tridiag_inv(const double* __restrict__ Dband, int n, int b,
+                                                     T* __restrict__ dinv, int* __restrict__ info) {
     extern __shared__ double sh[];
-    double* l = sh;       // l[k] = D[k,k-1] / u[k-1]
-    double* u = sh + b;   // pivots
+    double* l = sh;       // l[k] = D[k,k-1] / u[k-1]; holds D[k,k-1] until the recurrence
+    double* u = sh + b;   // pivots; holds D[k,k] until the recurrence
     double* du = sh + 2 * b;
     T* lt = reinterpret_cast<T*>(sh + 3 * b);  // l[k] in T
     T* rt = lt + b;                            // du[k-1] / u[k] in T
+    __shared__ double s_red[32];
     const int e = blockIdx.y, j = 2 * e;
     const double* Dl = Dband + (size_t)j * 3 * b;
     const double* Dd = Dl + b;
     const double* Du = Dd + b;
-    for (int k = threadIdx.x; k < b; k += blockDim.x) du[k] = (k + 1 < b) ? Du[k] : 0.0;
+    double amax = 0.0;
+    for (int k = threadIdx.x; k < b; k += blockDim.x) {
+        l[k] = Dl[k];
+        u[k] = Dd[k];
+        du[k] = (k + 1 < b) ? Du[k] : 0.0;
+        amax = fmax(amax, fabs(u[k]));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = amax;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double amax = 0.0;
-        for (int k = 0; k < b; ++k) amax = fmax(amax, fabs(Dd[k]));
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) amax = fmax(amax, s_red[w]);
         const double tiny = 16.0 * 2.220446049250313e-16 * amax;
         int bad = 0;
-        double up = Dd[0];
+        double up = u[0];
         l[0] = 0.0;
-        u[0] = up;
         if (!(fabs(up) > tiny)) bad = 1;
         for (int k = 1; k < b; ++k) {
-            const double lk = (up != 0.0) ? Dl[k] / up : 0.0;
-            up = Dd[k] - lk * Du[k - 1];
+            const double lk = (up != 0.0) ? l[k] / up : 0.0;
+            up = u[k] - lk * du[k - 1];
             l[k] = lk;
             u[k] = up;
             if (!bad && !(fabs(up) > tiny)) bad = k + 1;
         }
-        if (blockIdx.x == 0) info[e] = bad;
+        info[e] = bad;
     }
     __syncthreads();
     // per-element recurrences in the factor's precision, divisions hoisted
@@ -57,21 +67,35 @@ __global__ void k_tridiag_inv(const double* __restrict__ Dband, int n, int b, T*
         rt[k] = (k > 0 && u[k] != 0.0) ? (T)(du[k - 1] / u[k]) : T(0);
     }
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= b) return;
-    T* X = dinv + (size_t)e * b * b + r;
-    for (int c = 0; c < r; ++c) X[(size_t)c * b] = T(0);
-    T z = (u[r] != 0.0) ? (T)(1.0 / u[r]) : T(0);
-    X[(size_t)r * b] = z;
-    for (int c = r + 1; c < b; ++c) {
-        z = -rt[c] * z;
-        X[(size_t)c * b] = z;
-    }
-    T y = X[(size_t)(b - 1) * b];
-    for (int c = b - 2; c >= 0; --c) {
-        const T zc = (c >= r) ? X[(size_t)c * b] : T(0);
-        y = zc - lt[c + 1] * y;
-        X[(size_t)c * b] = y;
+    for (int r = threadIdx.x; r < b; r += blockDim.x) {
+        T* X = dinv + (size_t)e * b * b + r;
+        // forward: z_c for c >= r (the entries c < r are written by the backward pass)
+        T z = (u[r] != 0.0) ? (T)(1.0 / u[r]) : T(0);
+        X[(size_t)r * b] = z;
+        for (int c = r + 1; c < b; ++c) {
+            z = -rt[c] * z;
+            X[(size_t)c * b] = z;
+        }
+        // backward: y_c = z_c - l_{c+1} y_{c+1}.  The z_c are read back 32 at a
+        // time before the chunk's stores, so that one memory latency is paid per
+        // chunk rather than per column.
+        T y = X[(size_t)(b - 1) * b];
+        for (int c0 = b - 2; c0 >= 0; c0 -= 32) {
+            T zc[32];
+#pragma unroll
+            for (int u2 = 0; u2 < 32; ++u2) {
+                const int c = c0 - u2;
+                zc[u2] = (c >= 0 && c >= r) ? X[(size_t)c * b] : T(0);
+            }
+#pragma unroll
+            for (int u2 = 0; u2 < 32; ++u2) {
+                const int c = c0 - u2;
+                if (c >= 0) {
+                    y = zc[u2] - lt[c + 1] * y;
+                    X[(size_t)c * b] = y;
+                }
+            }
+        }
     }
 }
 
@@ -79,11 +103,10 @@ template <class T>
 cudaError_t tridiag_inverse(const double* Dband, int n, int b, T* dinv, int* info, cudaStream_t s) {
     const int ne = (n + 1) / 2;
     if (ne <= 0) return cudaSuccess;
-    dim3 g((b + 127) / 128, ne);
+    const int nt = b >= 512 ? 512 : ((b + 31) / 32) * 32;
     const size_t sm = 3 * (size_t)b * sizeof(double) + 2 * (size_t)b * sizeof(T);
-    if (sm > 48 * 1024)
-        ensure_smem((const void*)k_tridiag_inv<T>, sm);
-    k_tridiag_inv<T><<<g, 128, sm, s>>>(Dband, n, b, dinv, info);
+    if (sm > 48 * 1024) ensure_smem((const void*)k_tridiag_inv<T>, sm);
+    k_tridiag_inv<T><<<dim3(1, ne), nt, sm, s>>>(Dband, n, b, dinv, info);
     count_launches(1);
     return cudaGetLastError();
 }
