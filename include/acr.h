@@ -112,7 +112,8 @@ void acr_default_opts(acr_opts *o);
 /* Factor (reduction phase of Section 3) with default options.
  *  nblk, blksz >= 1.  tol <= 0: uncompressed blocks (dense block cyclic
  *  reduction, FP64).  tol > 0: blocks stored in HODLR form with off-diagonal
- *  ranks truncated at sigma_k > tol * sigma_1 of each node.
+ *  ranks truncated at sigma_k > max(tol, c eps) * sigma_1 of each node (eps
+ *  of the factor's precision; c = 8 for FP32 factors, 32 for FP64).
  *  On success *out receives a handle that keeps the factorization on the GPU
  *  until acr_free. */
 int acr_factor(int nblk, int blksz, const double *A, const double *D, const double *C,
@@ -125,7 +126,10 @@ int acr_factor_ex(int nblk, int blksz, const double *A, const double *D, const d
 /* Solve M X = B in place (forward reduction + back-substitution of Section 3,
  * refinement in the mixed-precision modes).  B: N x nrhs, overwritten with X.
  * nrhs >= 0.  Solves on one handle may run concurrently from several host
- * threads: each call uses its own workspace. */
+ * threads: each call uses its own workspace.  From its second preconditioner
+ * application on, a solve replays its sweeps as a CUDA graph captured on the
+ * handle's stream (not on the legacy NULL stream, nor on a stream that is
+ * already being captured, where the same launches are issued directly). */
 int acr_solve(acr_handle h, double *B, int nrhs);
 
 /* As acr_solve, also returning per column the final relative residual

@@ -611,8 +611,8 @@ cudaError_t node_svd(const T* Y, T* U, T* sig, int nnodes, int s, int k, cudaStr
 
 // ---------------------------------------------------------------- packing
 // node i: rank r = meta[i].rank (-1: dense), destination offset meta[i].off;
-// U_k, V_k (s x k) or the dense block (src pointer, ld b).
-__global__ void k_dummy() {}
+// U_k, V_k (s x k) or the dense block (src pointer, ld b); rank -2: packed by
+// another launch.
 
 template <class T>
 __global__ void k_pack_nodes(const HNode* __restrict__ meta, int node0, const T* __restrict__ Uk,
