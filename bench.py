@@ -185,18 +185,18 @@ def measured_peaks():
         return None
 
 
-def traffic_record(kernel):
+def traffic_record(kernel, root=ROOT):
     """The committed ncu DRAM-traffic record of `kernel`, or None when there is
     none or the kernel's source changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(root, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get("k_" + kernel)
     except (OSError, ValueError):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1604_00617_gb300", "csrc", "k_tc.cu")
+    src = os.path.join(root, "paper_1604_00617_gb300", "csrc", "k_tc.cu")
     try:
         if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec.get("source_sha1"):
             return None
