@@ -1248,10 +1248,16 @@ int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
                 if (g) cudaGraphDestroy(g);
                 return st;
             }
-            CK(ee);
-            const cudaError_t ei = cudaGraphInstantiate(&sp.gexec, g, 0);
-            cudaGraphDestroy(g);
-            CK(ei);
+            // a capture or instantiation the driver refuses is not an error of
+            // the solve: launch directly from now on
+            cudaError_t ei = ee;
+            if (ee == cudaSuccess) ei = cudaGraphInstantiate(&sp.gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                cudaGetLastError();
+                sp.gexec = nullptr;
+                sp.no_graph = true;
+            }
         }
     }
     CK(cudaEventRecord(e0, s));
