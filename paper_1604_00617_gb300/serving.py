@@ -358,6 +358,26 @@ def serve(nreq: int = 2000, rate: float = 100.0, seed: int = 42, budget_gb: floa
     return out
 
 
+def capacity_sweep(events, rate: float, fractions=(0.5, 0.8, 1.0), serve_fn=None):
+    """Capacity, then offered loads relative to it: the mix is served with
+    every request arriving at t = 0 (capacity = requests / wall time), then
+    with its arrival times rescaled to each fraction of that capacity.
+    `events` were drawn at `rate` requests/s; `serve_fn(events, rate)` returns
+    a summary with "wall_s" (serve() with the defaults).  Returns
+    (capacity, [summary per fraction])."""
+    serve_fn = serve_fn or (lambda ev, r: serve(rate=r, events=ev))
+    burst = [(0.0, dataclasses.replace(r, arrival=0.0)) for _, r in events]
+    first = serve_fn(burst, float("inf"))
+    capacity = len(events) / first["wall_s"]
+    out = []
+    for f in fractions:
+        sm = serve_fn(_rescale(events, rate, f * capacity), f * capacity)
+        sm["capacity_fraction"] = f
+        sm["capacity_rps"] = capacity
+        out.append(sm)
+    return capacity, out
+
+
 def _rescale(events, rate_from: float, rate_to: float):
     """The same requests with arrival times scaled to another offered rate."""
     k = rate_from / rate_to
@@ -378,9 +398,19 @@ if __name__ == "__main__":
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--capacity", type=str, default="",
+                    help="comma-separated fractions of the measured capacity to offer instead of --rates")
     a = ap.parse_args()
     rates = [float(x) for x in a.rates.split(",")]
     base = make_requests(a.requests, rates[0], a.seed)
+    if a.capacity:
+        fr = [float(x) for x in a.capacity.split(",")]
+        cap, res = capacity_sweep(base, rates[0], fr, lambda ev, r: serve(
+            rate=r, budget_gb=a.budget_gb, slots=a.slots, max_batch=a.max_batch, events=ev))
+        print(json.dumps({"capacity_requests_per_s": cap}), flush=True)
+        for sm in res:
+            print(json.dumps(sm), flush=True)
+        raise SystemExit(0)
     for rate in rates:
         ev = base if rate == rates[0] else _rescale(base, rates[0], rate)
         print(json.dumps(serve(rate=rate, budget_gb=a.budget_gb, slots=a.slots, max_batch=a.max_batch, events=ev)),

@@ -177,3 +177,21 @@ def test_request_stream_seeded():
         solves = [r for _, r in e1 if isinstance(r, serving.SolveRequest) and r.sys_rid == s.rid]
         assert len(solves) == s.nsolve >= 1
         assert s.leaf == 32 and s.tol == 1e-6
+
+
+def test_capacity_sweep_rescales_arrivals():
+    ev = serving.make_requests(24, rate=100.0, seed=1, sizes=(8,), probs=(1.0,), max_solves=4)
+    seen = []
+
+    def fake_serve(events, rate):
+        seen.append((rate, [t for t, _ in events]))
+        return {"wall_s": 2.0 if rate == float("inf") else 1.0}
+
+    cap, res = serving.capacity_sweep(ev, 100.0, (0.5, 1.0), fake_serve)
+    assert cap == pytest.approx(len(ev) / 2.0)
+    assert seen[0][1] == [0.0] * len(ev)                       # the burst
+    t0 = [t for t, _ in ev]
+    for (rate, ts), f in zip(seen[1:], (0.5, 1.0)):
+        assert rate == pytest.approx(f * cap)
+        assert ts == pytest.approx([t * 100.0 / (f * cap) for t in t0])
+    assert [r["capacity_fraction"] for r in res] == [0.5, 1.0]
