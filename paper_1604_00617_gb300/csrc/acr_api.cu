@@ -113,6 +113,23 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// CUDA events owned by one call, destroyed on every return path (an event
+// still pending on a stream is released once it completes).
+struct Events {
+    std::vector<cudaEvent_t> all;
+    Events() = default;
+    Events(const Events&) = delete;
+    Events& operator=(const Events&) = delete;
+    ~Events() {
+        for (cudaEvent_t e : all) cudaEventDestroy(e);
+    }
+    cudaError_t make(cudaEvent_t* e) {
+        const cudaError_t r = cudaEventCreate(e);
+        if (r == cudaSuccess) all.push_back(*e);
+        return r;
+    }
+};
+
 }  // namespace
 
 struct acr_ctx {
@@ -727,9 +744,10 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         }
     }
 
+    Events evown;
     cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    CK(evown.make(&e0));
+    CK(evown.make(&e1));
     CK(cudaEventRecord(e0, s));
 
     // ---- level 0 staging -----------------------------------------------------
@@ -752,7 +770,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     std::vector<int> evcls;  // 0: inversion, 1: products
     auto mark = [&](int cls) -> cudaError_t {
         cudaEvent_t e;
-        cudaError_t err = cudaEventCreate(&e);
+        cudaError_t err = evown.make(&e);
         if (err != cudaSuccess) return err;
         evs.push_back(e);
         evcls.push_back(cls);
@@ -805,8 +823,6 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (tc) {
         int terr = 0;
         CK(cudaMemcpy(&terr, dterr.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -824,7 +840,6 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         cudaEventElapsedTime(&d, evs[i], evs[i + 1]);
         cls_ms[evcls[i]] += d;
     }
-    for (cudaEvent_t e : evs) cudaEventDestroy(e);
     h->st.factor_ms = ms;
     // structured level 0: O(b^2) per block (tridiagonal inverse: ~3 b^2;
     // elementwise Schur complement: ~8 b^2 per kept block)
@@ -847,8 +862,8 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     if (h->tol > 0) {
         const long long c0 = launch_count();
         cudaEvent_t ce0, ce1;
-        CK(cudaEventCreate(&ce0));
-        CK(cudaEventCreate(&ce1));
+        CK(evown.make(&ce0));
+        CK(evown.make(&ce1));
         CK(cudaEventRecord(ce0, s));
         const int st = compress_factor<T>(h);
         if (st != ACR_OK) return st;
@@ -856,8 +871,6 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         CK(cudaEventSynchronize(ce1));
         float cms = 0.f;
         cudaEventElapsedTime(&cms, ce0, ce1);
-        cudaEventDestroy(ce0);
-        cudaEventDestroy(ce1);
         h->st.factor_ms += cms;
         h->st.launches_factor += launch_count() - c0;
     }
@@ -1213,16 +1226,16 @@ int issue_sweep(acr_ctx* h, SweepPlan<T>& sp) {
 }
 
 // One application of the sweeps.  The launch sequence of a plan never changes
-// (fixed buffers), so it is captured into a CUDA graph at the first
-// application and replayed afterwards -- unless the caller's stream is itself
-// being captured, where the launches are issued directly.
+// (fixed buffers), so it is captured into a CUDA graph at the second
+// application and replayed afterwards -- except on the NULL stream or a stream
+// the caller is capturing, where the launches are issued directly.
 template <class T>
 int run_sweep(acr_ctx* h, SweepPlan<T>& sp) {
     cudaStream_t s = h->stream;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
     sp.evs.push_back(e0);
+    CK(cudaEventCreate(&e1));
     sp.evs.push_back(e1);
     // capture from the second application on: a plan used once is never
     // captured, and every kernel's shared-memory limit has been raised by then
@@ -1555,9 +1568,10 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
     const bool dev = is_device_ptr(B);
     DevBuf dB;
     double* f = B;
+    Events evown;
     cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    CK(evown.make(&e0));
+    CK(evown.make(&e1));
     if (!dev) {
         CK(dB.alloc(bytes, s));
         CK(cudaMemcpyAsync(dB.p, B, bytes, cudaMemcpyHostToDevice, s));
@@ -1602,8 +1616,6 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
     CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(h->mu);
         h->st.solve_ms = ms;
