@@ -174,6 +174,12 @@ int acr_stats(acr_handle h, acr_stats_t *s);
  * under a memory budget. */
 int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts *o, size_t *bytes);
 
+/* Upper bound of the device bytes one acr_solve_ex call allocates for its
+ * workspace (FGMRES bases, sweep vectors, partial sums) for nrhs right-hand
+ * sides with these options; the factorization's own bytes are not included.
+ * Used, with acr_factor_bytes, for admission under a memory budget. */
+int acr_solve_bytes(int nblk, int blksz, int nrhs, const acr_opts *o, size_t *bytes);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *acr_last_error(void);
 

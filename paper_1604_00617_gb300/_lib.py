@@ -44,7 +44,8 @@ _NAMES = {0: "ACR_OK", -1: "ACR_ERR_INVALID_ARG", -2: "ACR_ERR_OOM", -3: "ACR_ER
 
 # every symbol include/acr.h declares
 EXPORTED = ["acr_default_opts", "acr_factor", "acr_factor_ex", "acr_solve", "acr_solve_ex",
-            "acr_free", "acr_stats", "acr_factor_bytes", "acr_last_error", "acr_block_inverse_noalloc"]
+            "acr_free", "acr_stats", "acr_factor_bytes", "acr_solve_bytes", "acr_last_error",
+            "acr_block_inverse_noalloc"]
 
 # fixed scratch of acr_block_inverse_noalloc (ACR_NOALLOC_SCRATCH_BYTES)
 ACR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.acr_factor_bytes.argtypes = [i, i, ctypes.c_double, ctypes.POINTER(acr_opts),
                                      ctypes.POINTER(ctypes.c_size_t)]
     lib.acr_factor_bytes.restype = i
+    lib.acr_solve_bytes.argtypes = [i, i, i, ctypes.POINTER(acr_opts), ctypes.POINTER(ctypes.c_size_t)]
+    lib.acr_solve_bytes.restype = i
     lib.acr_last_error.argtypes = []
     lib.acr_last_error.restype = ctypes.c_char_p
     lib.acr_block_inverse_noalloc.argtypes = [i, i, vp, vp, vp]
@@ -220,6 +223,13 @@ def acr_factor_bytes(nblk: int, blksz: int, tol: float = 0.0, opts: acr_opts | N
     o = opts if opts is not None else acr_default_opts()
     out = ctypes.c_size_t(0)
     _check(_lib.acr_factor_bytes(nblk, blksz, float(tol), ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def acr_solve_bytes(nblk: int, blksz: int, nrhs: int, opts: acr_opts | None = None) -> int:
+    o = opts if opts is not None else acr_default_opts()
+    out = ctypes.c_size_t(0)
+    _check(_lib.acr_solve_bytes(nblk, blksz, nrhs, ctypes.byref(o), ctypes.byref(out)))
     return out.value
 
 

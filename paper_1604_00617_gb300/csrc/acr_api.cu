@@ -1657,6 +1657,22 @@ int acr_factor_bytes(int nblk, int blksz, double tol, const acr_opts* o, size_t*
     return ACR_OK;
 }
 
+int acr_solve_bytes(int nblk, int blksz, int nrhs, const acr_opts* o, size_t* bytes) {
+    if (nblk < 1 || blksz < 1 || nrhs < 0 || !bytes) return fail(ACR_ERR_INVALID_ARG, "bad arguments");
+    acr_opts op;
+    if (o) op = *o; else default_opts(&op);
+    const size_t es = op.precision == ACR_FP64 ? 8 : 4;
+    const size_t NQ = (size_t)nblk * blksz * (size_t)nrhs;
+    const int maxit = op.ir_max_iter > 0 ? op.ir_max_iter : 20;
+    const size_t m = op.refine == ACR_REFINE_FGMRES ? (size_t)std::min(ACR_FGMRES_RESTART, maxit) : 0;
+    // FP64 vectors: staged B, x, r, z, w and the FGMRES bases V (m + 1) and Z (m);
+    // factor-precision vectors: the preconditioner's input, its level vectors
+    // (about 2), the node products of the compressed apply (bounded by 2) and
+    // the direct sweep's of FP64 mode (2); Gram-Schmidt partials; tables
+    *bytes = NQ * (8 * (2 * m + 6) + 7 * es) + 2 * (size_t)64 * 1024 * 8 * nrhs + ((size_t)64 << 20);
+    return ACR_OK;
+}
+
 }  // extern "C"
 
 namespace {

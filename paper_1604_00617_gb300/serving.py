@@ -9,8 +9,9 @@ factorization.  The loop
   has room for the factorization's peak working set (a bound computed from
   ``acr_factor_bytes``); the reservation shrinks to the bytes the handle
   keeps once the factorization returns (the compressed size when tol > 0).
-  Requests that arrive while others run are admitted as slots and memory free
-  up -- nothing waits for the current batch to drain;
+  Every solve call reserves its workspace (``acr_solve_bytes``) while it
+  runs.  Requests that arrive while others run are admitted as slots and
+  memory free up -- nothing waits for the current batch to drain;
 * runs each admitted piece of work in its own host thread (the C calls drop
   the Python lock) on the stream of its system, every resident system having
   a stream of its own, so factorizations and solves of different systems
@@ -105,6 +106,15 @@ def peak_bytes(req: SystemRequest, precision: int) -> int:
     return int(est)
 
 
+def solve_bytes(nblk: int, blksz: int, nrhs: int, precision: int, ir_max_iter: int) -> int:
+    """Upper bound of one solve call's device workspace (acr_solve_bytes)."""
+    o = acr.acr_default_opts()
+    o.precision = precision
+    o.input_kind = acr.ACR_BANDED
+    o.ir_max_iter = ir_max_iter
+    return acr.acr_solve_bytes(nblk, blksz, nrhs, o)
+
+
 class Server:
     """Admission by memory budget, resident factorizations, solve batching."""
 
@@ -134,6 +144,8 @@ class Server:
         self.active = 0
         self.peak_active = 0
         self.handles = {}            # sys rid -> (handle, bytes held, stream)
+        self.dims = {}               # sys rid -> (nblk, blksz)
+        self.solving = 0             # solve calls in flight
         self.pending = collections.defaultdict(collections.deque)
         self.remaining = {}          # sys rid -> solves still to serve
         self.busy = set()            # systems with a solve batch in flight
@@ -199,7 +211,7 @@ class Server:
             rec = self.records[r.rid]
             rec.ok, rec.done = False, time.perf_counter()
 
-    def _run_solves(self, sys_rid: int, batch: list):
+    def _run_solves(self, sys_rid: int, batch: list, ws: int):
         h = self.handles[sys_rid][0]
         t0 = time.perf_counter()
         B = np.asfortranarray(np.stack([r.rhs for r in batch], axis=1))
@@ -220,6 +232,8 @@ class Server:
                 self.results[r.rid] = B[:, q].copy()
         with self.cv:
             self.busy.discard(sys_rid)
+            self.reserved -= ws
+            self.solving -= 1
             self.remaining[sys_rid] -= len(batch)
             if self.remaining[sys_rid] == 0:
                 self._release(sys_rid)
@@ -229,22 +243,37 @@ class Server:
     def _dispatch(self):
         """Start whatever can start now (called with the lock held)."""
         started = []
-        # solve batches first: finishing a system frees its memory
+        # solve batches first: finishing a system frees its memory.  A batch
+        # reserves its workspace; it is halved until that fits the budget, and
+        # runs over budget only when no other solve is in flight (resident
+        # factorizations free their memory only after their solves)
         for sys_rid, q in list(self.pending.items()):
             if self.active >= self.slots:
                 break
             if q and sys_rid in self.handles and sys_rid not in self.busy:
-                batch = [q.popleft() for _ in range(min(len(q), self.max_batch))]
+                nblk, blksz = self.dims[sys_rid]
+                nb = min(len(q), self.max_batch)
+                ws = solve_bytes(nblk, blksz, nb, self.precision, self.ir_max_iter)
+                while nb > 1 and self.reserved + ws > self.budget:
+                    nb = (nb + 1) // 2
+                    ws = solve_bytes(nblk, blksz, nb, self.precision, self.ir_max_iter)
+                if self.reserved + ws > self.budget and self.solving > 0:
+                    continue
+                batch = [q.popleft() for _ in range(nb)]
                 self.busy.add(sys_rid)
                 self.active += 1
+                self.solving += 1
+                self.reserved += ws
+                self.peak_reserved = max(self.peak_reserved, self.reserved)
                 self.peak_active = max(self.peak_active, self.active)
-                started.append(threading.Thread(target=self._run_solves, args=(sys_rid, batch)))
+                started.append(threading.Thread(target=self._run_solves, args=(sys_rid, batch, ws)))
         while self.sys_queue and self.active < self.slots:
             req = self.sys_queue[0]
             est = peak_bytes(req, self.precision)
             if self.reserved + est > self.budget and self.reserved > 0:
                 break  # wait until memory is released (admission stays in arrival order)
             self.sys_queue.popleft()
+            self.dims[req.rid] = (req.nblk, req.blksz)
             self.reserved += est
             self.peak_reserved = max(self.peak_reserved, self.reserved)
             self.active += 1

@@ -73,3 +73,20 @@ def test_factor_bytes_plan(lib):
     o.precision = lib.ACR_FP32_IR
     o.input_kind = lib.ACR_BANDED
     assert lib.acr_factor_bytes(8, 4, 0.0, o) == plan(4) + 5 * 32 * 8
+
+
+def test_solve_bytes_bound(lib):
+    o = lib.acr_default_opts()
+    o.precision = lib.ACR_FP32TC_IR
+    o.ir_max_iter = 60                       # restart length 50
+    N = 64 * 64
+    b1 = lib.acr_solve_bytes(64, 64, 1, o)
+    b8 = lib.acr_solve_bytes(64, 64, 8, o)
+    assert b8 > b1 > 0
+    assert b8 >= N * 8 * 8 * (50 + 51)       # the FGMRES bases V and Z alone
+    o.refine = lib.ACR_REFINE_IR             # no Krylov bases
+    assert lib.acr_solve_bytes(64, 64, 8, o) < b8
+    with pytest.raises(lib.AcrError):
+        lib.acr_solve_bytes(0, 64, 1, o)
+    with pytest.raises(lib.AcrError):
+        lib.acr_solve_bytes(64, 64, -1, o)

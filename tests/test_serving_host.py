@@ -195,3 +195,23 @@ def test_capacity_sweep_rescales_arrivals():
         assert rate == pytest.approx(f * cap)
         assert ts == pytest.approx([t * 100.0 / (f * cap) for t in t0])
     assert [r["capacity_fraction"] for r in res] == [0.5, 1.0]
+
+
+def test_solve_workspace_counts_against_budget():
+    # room for the factorization, then for the resident factor (1 MB in the
+    # fake) plus the workspace of 4 right-hand sides -- not of 16
+    lib = FakeLib(tf=0.05, ts=0.01)
+    n = 64
+    req = _system(0, 0.0, n, 0)
+    fac = serving.peak_bytes(req, acr.ACR_FP32TC_IR)
+    four = serving.solve_bytes(n, n, 4, acr.ACR_FP32TC_IR, 60)
+    assert serving.solve_bytes(n, n, 8, acr.ACR_FP32TC_IR, 60) > four
+    budget = max(fac, lib.held + four)
+    ev = _stream([(0.0, n, [0.001 * (i + 1) for i in range(16)])])
+    srv = serving.Server(budget, slots=2, lib=lib, new_stream=FakeStream, max_batch=64)
+    recs, _ = srv.run(ev)
+    assert all(r.ok for r in recs.values())
+    assert sum(c[1] for c in lib.solve_calls) == 16
+    assert max(c[1] for c in lib.solve_calls) < 16      # batches were cut to fit
+    assert srv.peak_reserved <= budget
+    assert srv.reserved == 0
