@@ -1542,39 +1542,57 @@ __global__ void k_multi_dot_partial(const double* __restrict__ V, const double* 
 
 // grid (chunks, nrhs): one CTA per chunk of DW = 16 x 256 rows holds its
 // rows of w in registers and forms all nvec partial products from them
-// (w read once, 16 independent loads of V in flight per thread);
-// ws[(i * nrhs + q) * chunks + c] as k_multi_dot_partial.
+// (w read once, 16 independent loads of V in flight per thread, the loads of
+// vector i + 1 issued before the partial sum of vector i is reduced).  Each
+// warp reduces its partial by shuffles and leaves it in shared memory, with
+// no barrier between vectors; the 8 warp partials of a vector are added in
+// warp order at the end.  ws[(i * nrhs + q) * chunks + c] as
+// k_multi_dot_partial.
 constexpr int DW = 16;
+constexpr int DOT_VB = 64;  // vectors per shared-memory batch
 __global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ V, int nvec,
                                                      const double* __restrict__ w, long long N, int nrhs,
                                                      double* __restrict__ ws) {
-    __shared__ double red[8];
-    const int q = blockIdx.y, chunks = gridDim.x, tid = threadIdx.x;
+    __shared__ double red[DOT_VB * 8];
+    const int q = blockIdx.y, chunks = gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long lo = (long long)blockIdx.x * DW * 256;
     const double* wq = w + (long long)q * N;
-    double wr[DW];
+    double wr[DW], v[DW];
 #pragma unroll
     for (int u = 0; u < DW; ++u) {
         const long long r = lo + tid + u * 256;
         wr[u] = r < N ? wq[r] : 0.0;
     }
-    for (int i = 0; i < nvec; ++i) {
-        const double* vq = V + ((long long)i * nrhs + q) * N;
-        double v[DW];
+    if (nvec > 0) {
+        const double* vq = V + (long long)q * N;
 #pragma unroll
         for (int u = 0; u < DW; ++u) {
             const long long r = lo + tid + u * 256;
             v[u] = r < N ? vq[r] : 0.0;
         }
-        double sum = 0.0;
+    }
+    for (int i0 = 0; i0 < nvec; i0 += DOT_VB) {
+        const int i1 = min(nvec, i0 + DOT_VB);
+        for (int i = i0; i < i1; ++i) {
+            double sum = 0.0;
 #pragma unroll
-        for (int u = 0; u < DW; ++u) sum = fma(v[u], wr[u], sum);
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if ((tid & 31) == 0) red[tid >> 5] = sum;
+            for (int u = 0; u < DW; ++u) sum = fma(v[u], wr[u], sum);
+            if (i + 1 < nvec) {
+                const double* vq = V + ((long long)(i + 1) * nrhs + q) * N;
+#pragma unroll
+                for (int u = 0; u < DW; ++u) {
+                    const long long r = lo + tid + u * 256;
+                    v[u] = r < N ? vq[r] : 0.0;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) red[(i - i0) * 8 + warp] = sum;
+        }
         __syncthreads();
-        if (tid == 0) {
+        for (int i = i0 + tid; i < i1; i += 256) {
             double t = 0.0;
-            for (int k = 0; k < 8; ++k) t += red[k];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += red[(i - i0) * 8 + k];
             ws[((long long)i * nrhs + q) * chunks + blockIdx.x] = t;
         }
         __syncthreads();
