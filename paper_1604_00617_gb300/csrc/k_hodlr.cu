@@ -23,6 +23,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "acr_internal.h"
 
@@ -139,10 +140,168 @@ k_gemm_gen(const T* const* __restrict__ Ap, const T* const* __restrict__ Bp, T* 
     }
 }
 
+// Thin batched product for the sketch widths (FP32, N <= 32): one thread owns
+// TM rows of C (rows t, t + RT, ...) and all NP >= N of its columns.  Its
+// entries of op(A) come straight from global memory -- for op(A) = A a warp
+// reads 32 consecutive rows of one column, for op(A) = A^T each thread reads
+// runs of KU consecutive k of its own column, as float4 when aligned -- and
+// B (K x N) is staged once per CTA in shared memory and read back as 16-byte
+// broadcasts (chunks of 4 columns, the chunk index XOR-ed with k so that the
+// staging stores spread over the banks).  Every k costs one shared load per
+// 4 x TM FMAs.  For small M the CTA's threads split K into KS = 128 / RT
+// ranges whose partial sums are added in range order.
+constexpr int THIN_NT = 128, THIN_TM = 2, THIN_KU = 16;
+
+template <int NP>
+__device__ __forceinline__ int thin_bs(int k, int c) {
+    return k * NP + ((((c >> 2) ^ k) & (NP / 4 - 1)) << 2) + (c & 3);
+}
+
+template <bool TA, int NP>
+__global__ void __launch_bounds__(THIN_NT)
+k_gemm_thin(const float* const* __restrict__ Ap, const float* const* __restrict__ Bp, float* const* __restrict__ Cp,
+            int M, int N, int K, int lda, int ldb, int ldc, int RT) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TM = THIN_TM, KU = THIN_KU;
+    const int KP = (K + 7) & ~7;                      // staged rows of B (zero beyond K)
+    float* Bs = reinterpret_cast<float*>(smem_raw);  // KP x NP, swizzled
+    float* red = Bs + (size_t)KP * NP;               // (KS - 1) x NP x (RT * TM) partial sums
+    const float* A = Ap[blockIdx.y];
+    const float* B = Bp[blockIdx.y];
+    float* C = Cp[blockIdx.y];
+    const int tid = threadIdx.x, KS = THIN_NT / RT, g = tid / RT, t = tid % RT;
+    const int R0 = blockIdx.x * RT * TM;
+    // stage B: a warp covers 8 consecutive k of 4 consecutive columns
+    for (int i = tid; i < KP * NP; i += THIN_NT) {
+        const int c = (i >> 3) % NP, k = ((i >> 3) / NP) * 8 + (i & 7);
+        Bs[thin_bs<NP>(k, c)] = (k < K && c < N) ? B[k + (size_t)c * ldb] : 0.f;
+    }
+    __syncthreads();
+    const int kper = (((K + KS - 1) / KS) + KU - 1) / KU * KU;
+    const int kb = min(K, g * kper), ke = min(K, kb + kper);
+    int row[TM];
+    bool live[TM];
+#pragma unroll
+    for (int j = 0; j < TM; ++j) {
+        row[j] = R0 + t + j * RT;
+        live[j] = row[j] < M;
+    }
+    const bool vec = TA && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && ((lda & 3) == 0);
+    float acc[TM][NP];
+#pragma unroll
+    for (int j = 0; j < TM; ++j)
+#pragma unroll
+        for (int c = 0; c < NP; ++c) acc[j][c] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += KU) {
+        float a[TM][KU];
+        if (TA) {
+#pragma unroll
+            for (int j = 0; j < TM; ++j) {
+                const float* col = A + (size_t)(live[j] ? row[j] : 0) * lda + k0;
+                if (vec && live[j] && k0 + KU <= ke) {
+#pragma unroll
+                    for (int v = 0; v < KU / 4; ++v) {
+                        const float4 x = reinterpret_cast<const float4*>(col)[v];
+                        a[j][4 * v] = x.x;
+                        a[j][4 * v + 1] = x.y;
+                        a[j][4 * v + 2] = x.z;
+                        a[j][4 * v + 3] = x.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KU; ++u) a[j][u] = (live[j] && k0 + u < ke) ? col[u] : 0.f;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < KU; ++u)
+#pragma unroll
+                for (int j = 0; j < TM; ++j)
+                    a[j][u] = (live[j] && k0 + u < ke) ? A[row[j] + (size_t)(k0 + u) * lda] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+            const int k = k0 + u;
+            if (k >= ke) break;
+#pragma unroll
+            for (int cc = 0; cc < NP / 4; ++cc) {
+                const float4 bv = *reinterpret_cast<const float4*>(Bs + k * NP + (((cc ^ k) & (NP / 4 - 1)) << 2));
+#pragma unroll
+                for (int j = 0; j < TM; ++j) {
+                    acc[j][4 * cc] = fmaf(a[j][u], bv.x, acc[j][4 * cc]);
+                    acc[j][4 * cc + 1] = fmaf(a[j][u], bv.y, acc[j][4 * cc + 1]);
+                    acc[j][4 * cc + 2] = fmaf(a[j][u], bv.z, acc[j][4 * cc + 2]);
+                    acc[j][4 * cc + 3] = fmaf(a[j][u], bv.w, acc[j][4 * cc + 3]);
+                }
+            }
+        }
+    }
+    if (KS > 1) {
+        const int RR = RT * TM;
+        if (g > 0)
+#pragma unroll
+            for (int j = 0; j < TM; ++j)
+#pragma unroll
+                for (int c = 0; c < NP; ++c) red[((size_t)(g - 1) * NP + c) * RR + t + j * RT] = acc[j][c];
+        __syncthreads();
+        if (g == 0)
+            for (int gg = 1; gg < KS; ++gg)
+#pragma unroll
+                for (int j = 0; j < TM; ++j)
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) acc[j][c] += red[((size_t)(gg - 1) * NP + c) * RR + t + j * RT];
+    }
+    if (g == 0)
+#pragma unroll
+        for (int j = 0; j < TM; ++j)
+            if (live[j])
+#pragma unroll
+                for (int c = 0; c < NP; ++c)
+                    if (c < N) C[row[j] + (size_t)c * ldc] = acc[j][c];
+}
+
+// launches k_gemm_thin when it applies (FP32, N <= 32, B fits in shared
+// memory); returns false otherwise
+static bool gemm_thin(const float* const* A, const float* const* B, float* const* C, int nprob, int M, int N, int K,
+                      int lda, int ldb, int ldc, bool transA, cudaStream_t s) {
+    if (N > 32 || M < 1 || K < 1) return false;
+    int RT = 32;
+    while (RT < THIN_NT && RT * THIN_TM < M) RT *= 2;
+    const int KS = THIN_NT / RT, NP = N <= 16 ? 16 : 32;
+    const size_t sm = ((size_t)((K + 7) & ~7) * NP + (size_t)(KS - 1) * NP * RT * THIN_TM) * sizeof(float);
+    if (sm > 160 * 1024) return false;
+    const void* fn = transA ? (NP == 16 ? (const void*)k_gemm_thin<true, 16> : (const void*)k_gemm_thin<true, 32>)
+                            : (NP == 16 ? (const void*)k_gemm_thin<false, 16> : (const void*)k_gemm_thin<false, 32>);
+    if (sm > 48 * 1024) ensure_smem(fn, sm);
+    const int gx = (M + RT * THIN_TM - 1) / (RT * THIN_TM);
+    int done = 0;
+    while (done < nprob) {  // grid.y is limited to 65535
+        const int cnt = std::min(nprob - done, 65535);
+        dim3 g(gx, cnt);
+        if (transA) {
+            if (NP == 16)
+                k_gemm_thin<true, 16><<<g, THIN_NT, sm, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc, RT);
+            else
+                k_gemm_thin<true, 32><<<g, THIN_NT, sm, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc, RT);
+        } else {
+            if (NP == 16)
+                k_gemm_thin<false, 16><<<g, THIN_NT, sm, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc, RT);
+            else
+                k_gemm_thin<false, 32><<<g, THIN_NT, sm, s>>>(A + done, B + done, C + done, M, N, K, lda, ldb, ldc, RT);
+        }
+        count_launches(1);
+        done += cnt;
+    }
+    return true;
+}
+
 template <class T>
 cudaError_t gemm_gen(const T* const* A, const T* const* B, T* const* C, int nprob, int M, int N, int K, int lda,
                      int ldb, int ldc, bool transA, cudaStream_t s) {
     if (nprob <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        if (gemm_thin(A, B, C, nprob, M, N, K, lda, ldb, ldc, transA, s)) return cudaGetLastError();
+    }
     const int tiles = ((M + 63) / 64) * ((N + 31) / 32);
     int done = 0;
     while (done < nprob) {  // grid.y is limited to 65535
