@@ -14,6 +14,7 @@ from .pde import (  # noqa: F401
     convection_diffusion,
     helmholtz,
     random_blocks,
+    strip_kernel_blocks,
     make_config,
     rhs_uniform,
     CONFIGS,

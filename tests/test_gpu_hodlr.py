@@ -132,6 +132,60 @@ def test_compressed_then_refined_to_1e8(lib, prec):
     assert (true_resid(P, X, F) <= 1.5e-8).all()
 
 
+def _factor_dense(lib, A, D, C, tol, prec, **kw):
+    o = lib.acr_default_opts()
+    o.precision = prec
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return lib.acr_factor_ex(D.shape[0], D.shape[1], _cm(A), _cm(D), _cm(C), tol, o)
+
+
+def _dense_matvec(A, D, C, X):
+    n, b = D.shape[0], D.shape[1]
+    Xb = X.reshape(n, b, -1)
+    Y = np.einsum("irs,isq->irq", D, Xb)
+    Y[1:] += np.einsum("irs,isq->irq", A[1:], Xb[:-1])
+    Y[:-1] += np.einsum("irs,isq->irq", C[:-1], Xb[1:])
+    return Y.reshape(n * b, -1)
+
+
+def test_fp32_sketch_mid_ranks_large_nodes(lib):
+    """Nodes of 512 down to 64 rows whose ranks (13..28 at 1e-6) saturate the
+    16-column sketch and are resolved by the 32-column one.  The FP32 path
+    (thin sketch products, one or more CTAs per node, K split for small
+    nodes) must find the ranks the FP64 path finds, keep every node low-rank,
+    and give a compressed solve accurate to the tolerance."""
+    A, D, C = syn.strip_kernel_blocks(3, 1024, seed=5)
+    F = syn.rhs_uniform(3 * 1024, 2, 2005)
+    stats = {}
+    for prec in (lib.ACR_FP64, lib.ACR_FP32TC_IR):
+        h = _factor_dense(lib, A, D, C, 1e-6, prec, leaf=64, refine=lib.ACR_REFINE_NONE, ir_tol=1.0)
+        try:
+            stats[prec] = lib.acr_stats(h)
+            X, res, it = solve(lib, h, F)
+        finally:
+            lib.acr_free(h)
+        st = stats[prec]
+        assert st["compressed"] == 1 and st["levels"] == 2
+        # no node stored dense (rank = node size), none left at the first sketch
+        assert all(14 <= m <= 28 for m in st["rank_max"]), st["rank_max"]
+        tr = np.linalg.norm(F - _dense_matvec(A, D, C, X), axis=0) / np.linalg.norm(F, axis=0)
+        assert (tr <= 1e-4).all(), (prec, tr)
+    s64, s32 = stats[lib.ACR_FP64], stats[lib.ACR_FP32TC_IR]
+    for t in range(2):
+        assert abs(s32["rank_max"][t] - s64["rank_max"][t]) <= 2, (s32["rank_max"], s64["rank_max"])
+        assert abs(s32["rank_mean"][t] - s64["rank_mean"][t]) <= 1.5, (s32["rank_mean"], s64["rank_mean"])
+    # the FP32 factorization as the preconditioner of FGMRES
+    h = _factor_dense(lib, A, D, C, 1e-6, lib.ACR_FP32TC_IR, leaf=64)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all() and it <= 8, (res, it)
+    tr = np.linalg.norm(F - _dense_matvec(A, D, C, X), axis=0) / np.linalg.norm(F, axis=0)
+    assert (tr <= 1.5e-8).all(), tr
+
+
 def test_tiny_tol_matches_dense(lib):
     P = syn.make_config(2, 64)
     F = syn.rhs_uniform(P.N, 2, 2002)

@@ -87,3 +87,26 @@ def test_banded_matvec_matches_assembled():
     P = syn.make_config(2, 9)
     x = np.random.default_rng(0).standard_normal((P.N, 2))
     assert np.allclose(P.matvec(x), P.assemble() @ x)
+
+
+def _offdiag_rank(M, r0, c0, sz, tol):
+    s = np.linalg.svd(M[r0:r0 + sz, c0:c0 + sz], compute_uv=False)
+    return int((s > tol * s[0]).sum())
+
+
+def test_strip_kernel_mid_ranks():
+    # the regime the FP32 sketch test relies on: every off-diagonal node of
+    # D^-1 and of the top block's inverse has rank 13..28 at 1e-6, so the
+    # 16-column sketch saturates and the 32-column one resolves it
+    A, D, C = syn.strip_kernel_blocks(3, 1024, seed=5)
+    assert A.shape == D.shape == C.shape == (3, 1024, 1024)
+    assert not A[0].any() and not C[-1].any()
+    K = D[0] - (D[0, 0, 0] - 1.0) * np.eye(1024)  # K has a unit diagonal
+    assert np.linalg.eigvalsh(K).min() > 0  # K is SPD
+    Di = [np.linalg.inv(D[j]) for j in (0, 2)]
+    top = np.linalg.inv(D[1] - A[1] @ Di[0] @ C[0] - C[1] @ Di[1] @ A[2])
+    for M in (Di[0], Di[1], top):
+        for l in range(1, 5):
+            sz = 1024 >> l
+            for r0, c0 in ((0, sz), (sz, 0)):
+                assert 13 <= _offdiag_rank(M, r0, c0, sz, 1e-6) <= 28, (l, r0, c0)
