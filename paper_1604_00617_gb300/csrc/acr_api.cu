@@ -1453,9 +1453,10 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
     } else {
         // restarted FGMRES(m), right preconditioned, one Krylov space per column
         const int m = std::min(ACR_FGMRES_RESTART, maxit);
-        DevBuf V, Z;
+        DevBuf V, Z, hacc;
         CK(V.alloc((size_t)(m + 1) * NQ * 8, s));
         CK(Z.alloc((size_t)m * NQ * 8, s));
+        CK(hacc.alloc((size_t)(m + 1) * nrhs * 8, s));
         double* Vp = V.as<double>();
         double* Zp = Z.as<double>();
         std::vector<double> H((size_t)nrhs * (m + 1) * m), g((size_t)nrhs * (m + 1)), cs((size_t)nrhs * m),
@@ -1482,21 +1483,19 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
                 ++iters;
                 if ((st = op.mv(Zj))) return st;
                 double* w = wb.as<double>();
-                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                // classical Gram-Schmidt, twice; the coefficients stay on the
+                // device and column j of H (h1 + h2) comes back with the norm
+                for (int pass = 0; pass < 2; ++pass) {
                     CK(multi_dot(Vp, j + 1, w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
-                    CK(cudaMemcpyAsync(hh.data(), sq.p, (size_t)(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost, s));
-                    CK(cudaStreamSynchronize(s));
-                    for (int i = 0; i <= j; ++i)
-                        for (int q = 0; q < nrhs; ++q) {
-                            Hq(q, i, j) += hh[(size_t)i * nrhs + q];
-                            hh[(size_t)i * nrhs + q] = -hh[(size_t)i * nrhs + q];
-                        }
-                    CK(cudaMemcpyAsync(coef.p, hh.data(), (size_t)(j + 1) * nrhs * 8, cudaMemcpyHostToDevice, s));
+                    CK(gs_coef(sq.as<double>(), coef.as<double>(), hacc.as<double>(), (j + 1) * nrhs, pass == 0, s));
                     CK(multi_axpy(w, Vp, j + 1, coef.as<double>(), N, nrhs, s));
                 }
                 CK(col_sumsq(w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
+                CK(cudaMemcpyAsync(hh.data(), hacc.p, (size_t)(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost, s));
                 CK(cudaMemcpyAsync(hs.data(), sq.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; ++i)
+                    for (int q = 0; q < nrhs; ++q) Hq(q, i, j) = hh[(size_t)i * nrhs + q];
                 bool all = true;
                 for (int q = 0; q < nrhs; ++q) {
                     const double hn = std::sqrt(hs[q]);

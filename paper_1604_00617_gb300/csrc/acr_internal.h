@@ -235,6 +235,9 @@ cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, i
 //   w[r, q] += sum_i coef[i * nrhs + q] V_i[r, q]
 cudaError_t multi_axpy(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
                        cudaStream_t s);
+//   coef[i] = -h[i] and hacc[i] = (first ? 0 : hacc[i]) + h[i]   (i < n): one
+//   Gram-Schmidt pass's coefficients and the Hessenberg column they add to
+cudaError_t gs_coef(const double* h, double* coef, double* hacc, int n, bool first, cudaStream_t s);
 //   v[r, q] = w[r, q] * scale[q]
 cudaError_t col_scale(double* v, const double* w, const double* scale, long long N, int nrhs,
                       cudaStream_t s);

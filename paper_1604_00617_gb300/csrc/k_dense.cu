@@ -1645,6 +1645,22 @@ cudaError_t multi_axpy(double* w, const double* V, int nvec, const double* coef,
     return cudaGetLastError();
 }
 
+__global__ void k_gs_coef(const double* __restrict__ h, double* __restrict__ coef, double* __restrict__ hacc, int n,
+                          int first) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = h[i];
+        coef[i] = -v;
+        hacc[i] = (first ? 0.0 : hacc[i]) + v;
+    }
+}
+
+cudaError_t gs_coef(const double* h, double* coef, double* hacc, int n, bool first, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_gs_coef<<<(n + 255) / 256, 256, 0, s>>>(h, coef, hacc, n, first ? 1 : 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 __global__ void k_col_scale(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ sc,
                             long long N, int nrhs) {
     const long long total = N * nrhs;
