@@ -188,7 +188,10 @@ class Server:
             h = self.lib.acr_factor_ex(req.nblk, req.blksz, req.a, req.D3, req.c, req.tol, self._opts(req, stream))
             st = self.lib.acr_stats(h)
             held = int(st["factor_bytes"] + st["operator_bytes"])
-        except acr.AcrError as e:
+        except Exception as e:  # any failure fails the request; the loop's bookkeeping still runs
+            if h is not None:
+                self.lib.acr_free(h)
+                h = None
             rec.ok = False
             self.errors.append((req.rid, str(e)))
         rec.done = time.perf_counter()
@@ -212,23 +215,25 @@ class Server:
             rec.ok, rec.done = False, time.perf_counter()
 
     def _run_solves(self, sys_rid: int, batch: list, ws: int):
-        h = self.handles[sys_rid][0]
         t0 = time.perf_counter()
-        B = np.asfortranarray(np.stack([r.rhs for r in batch], axis=1))
-        ok = True
+        ok, B, res, it = True, None, None, 0
         try:
+            h = self.handles[sys_rid][0]
+            B = np.asfortranarray(np.stack([r.rhs for r in batch], axis=1))
             res, it = self.lib.acr_solve_ex(h, B, B.shape[1])
-        except acr.AcrError as e:
+        except Exception as e:  # any failure fails the batch; the loop's bookkeeping still runs
             ok = False
-            res = getattr(e, "resid", np.full(len(batch), np.nan))
+            res = getattr(e, "resid", None)
             it = getattr(e, "iters", 0)
             self.errors.append((sys_rid, str(e)))
+        if res is None or len(res) < len(batch):
+            res = np.full(len(batch), np.nan)
         t1 = time.perf_counter()
         for q, r in enumerate(batch):
             rec = self.records[r.rid]
             rec.start, rec.done, rec.ok = t0, t1, ok
             rec.resid, rec.iters, rec.batch = float(res[q]), it, len(batch)
-            if self.keep_results:
+            if self.keep_results and B is not None:
                 self.results[r.rid] = B[:, q].copy()
         with self.cv:
             self.busy.discard(sys_rid)

@@ -155,6 +155,51 @@ def test_failed_factor_fails_its_solves_only():
     assert len(srv.errors) == 1 and "planted" in srv.errors[0][1]
 
 
+class RaisingLib(FakeLib):
+    """FakeLib whose factor of block count `bad_factor`, statistics of
+    `bad_stats` and solve of `bad_solve` raise errors that are not the
+    library's own."""
+
+    def __init__(self, bad_factor, bad_stats, bad_solve, **kw):
+        super().__init__(**kw)
+        self.bad_factor, self.bad_stats, self.bad_solve = bad_factor, bad_stats, bad_solve
+
+    def acr_factor_ex(self, nblk, blksz, a, D3, c, tol, o):
+        if nblk == self.bad_factor:
+            raise MemoryError("planted host failure")
+        return super().acr_factor_ex(nblk, blksz, a, D3, c, tol, o)
+
+    def acr_stats(self, h):
+        if h["n"] == self.bad_stats:
+            raise RuntimeError("planted stats failure")
+        return super().acr_stats(h)
+
+    def acr_solve_ex(self, h, B, nrhs):
+        if h["n"] == self.bad_solve:
+            raise ValueError("planted solve failure")
+        return super().acr_solve_ex(h, B, nrhs)
+
+
+def test_unexpected_exceptions_fail_requests_not_the_loop():
+    lib = RaisingLib(bad_factor=12, bad_stats=10, bad_solve=8, tf=0.02, ts=0.005)
+    ev = _stream([(0.0, 12, [0.001]), (0.0, 10, [0.002]), (0.0, 8, [0.003, 0.004]), (0.0, 6, [0.005])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    done = []
+    th = threading.Thread(target=lambda: done.append(srv.run(ev)), daemon=True)
+    th.start()
+    th.join(timeout=20)
+    assert done, "serving loop did not finish"
+    recs, _ = done[0]
+    # system 0: factor raises; system 2: statistics raise; system 4: its
+    # solves raise (its factor is fine); system 7 is untouched
+    assert not any(recs[i].ok for i in (0, 1, 2, 3, 5, 6))
+    assert recs[4].ok and recs[7].ok and recs[8].ok
+    # the handle whose statistics failed was freed; nothing stays reserved
+    assert 2 in lib.freed
+    assert srv.reserved == 0 and srv.active == 0 and srv.solving == 0
+    assert len(srv.errors) == 3
+
+
 def test_summary():
     lib = FakeLib(tf=0.01, ts=0.005)
     ev = _stream([(0.0, 8, [0.001 * i for i in range(1, 6)])])
