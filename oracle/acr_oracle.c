@@ -87,7 +87,7 @@ static int lu_factor(int b, double *M, size_t ld, int *piv) {
     for (int k = 0; k < b; ++k) {
         int p = k;
         double best = fabs(EL(M, ld, k, k));
-        for (int r = k + 1; r < b; ++r) {
+        for (int r = k + 1; r < b && ORACLE_MUTANT != 7; ++r) {  /* mutant 7: no interchange */
             double v = fabs(EL(M, ld, r, k));
             if (v > best) { best = v; p = r; }
         }
@@ -258,7 +258,7 @@ static int reduce_level(level_t *cur, level_t *nxt, int b, int nrhs, int *bad) {
                    cur->F + (size_t)i * b + (size_t)q * ldF, b * sizeof(double));
         if (nrhs > 0) {
             gemm_sub(b, Ai, G + (size_t)em * b, (size_t)ne * b, nxt->F + (size_t)k * b, ldFn, nrhs);
-            if (i + 1 < m)
+            if (i + 1 < m && ORACLE_MUTANT != 5)                       /* mutant 5: dropped term */
                 gemm_sub(b, Ci, G + (size_t)ep * b, (size_t)ne * b, nxt->F + (size_t)k * b, ldFn, nrhs);
         }
     }
@@ -339,7 +339,9 @@ int oracle_bcr_solve(int n, int b, const double *A, const double *D, const doubl
                 for (int q = 0; q < nrhs; ++q)
                     memcpy(uj + q * ld, L->F + (size_t)j * b + q * ld, b * sizeof(double));
                 if (j > 0) gemm_sub(b, L->A + (size_t)j * bb, Ul + (size_t)(j - 1) * b, ld, uj, ld, nrhs);
-                if (j + 1 < ml) gemm_sub(b, L->C + (size_t)j * bb, Ul + (size_t)(j + 1) * b, ld, uj, ld, nrhs);
+                if (j + 1 < ml)                                /* mutant 6: wrong neighbour */
+                    gemm_sub(b, L->C + (size_t)j * bb, Ul + (size_t)(ORACLE_MUTANT == 6 && j > 0 ? j - 1 : j + 1) * b,
+                             ld, uj, ld, nrhs);
                 lu_solve(b, L->D + (size_t)j * bb, b, L->piv + (size_t)j * b, uj, ld, nrhs);
             }
             free(U);

@@ -59,6 +59,24 @@ def pin_dense(n, b, seed, symmetric=False):
     return max(_rel(X, np.linalg.solve(M, F)), _rel(X, oracle.dense_solve(M, F)))
 
 
+def pin_pivot(n, b, seed):
+    """Brute force on blocks that need row interchanges: every D_i of a
+    diagonally dominant system has its rows shifted cyclically by one and its
+    new diagonal set to zero, so each block is a dominant permutation pattern
+    whose LU needs a row swap at every step (Section 3 inverts each eliminated
+    block with partial pivoting).  A singular report counts as an infinite
+    error."""
+    A, D, C = syn.random_blocks(n, b, seed)
+    D = np.roll(D, 1, axis=1)
+    D[:, np.arange(b), np.arange(b)] = 0.0
+    F = np.random.default_rng(seed + 11).standard_normal((n * b, 2))
+    try:
+        X = oracle.bcr_solve(A, D, C, F)
+    except oracle.OracleSingular:
+        return math.inf
+    return _rel(X, np.linalg.solve(_assemble(A, D, C), F))
+
+
 def _thomas(lo, di, up, f):
     n = len(di)
     cp = np.zeros(n); dp = np.zeros(n)
@@ -276,7 +294,7 @@ def _all_pins():
     """Error figures of a fast subset of the pins (used by the mutation test)."""
     errs = [pin_dense(7, 3, 1), pin_dense(8, 4, 2), pin_scalar(9, 3), pin_eigen(8, 3, 5),
             pin_dst(11, 5, 2)[0], pin_dst(8, 6, 3)[0], pin_schur(7, 3, 4), pin_schur(8, 3, 5),
-            pin_manufactured(2, 16)]
+            pin_manufactured(2, 16), pin_pivot(7, 6, 3)]
     return errs
 
 
@@ -284,10 +302,17 @@ def test_pins_pass_on_real_oracle():
     assert max(_all_pins()) < 1e-10
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4])
+@pytest.mark.parametrize("n,b,seed", [(7, 6, 3), (8, 5, 4), (5, 9, 1)])
+def test_row_interchanges_brute_force(n, b, seed):
+    assert pin_pivot(n, b, seed) < 1e-10
+
+
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
 def test_pins_catch_planted_mistakes(mutant):
-    """Each planted mistake (dropped term, wrong sign, wrong index, transposed
-    operand) makes at least one pin fail."""
+    """Each planted mistake makes at least one pin fail: a dropped Schur term,
+    a wrong sign, a wrong index, a transposed operand, a dropped term of the
+    right-hand-side reduction, a wrong neighbour in the back-substitution,
+    and an LU without row interchanges."""
     oracle.use_mutant(mutant)
     try:
         errs = _all_pins()
