@@ -387,6 +387,7 @@ def run_ours(args):
             "iters": last["iters"], "resid_max": max(last["resid"]),
             "kernels": {"gemm_ms": last["gemm_ms"], "gemm_tflops": last["gemm_flops"] / last["gemm_ms"] / 1e9,
                         "inv_ms": last["inv_ms"], "inv_tflops": last["inv_flops"] / max(last["inv_ms"], 1e-9) / 1e9,
+                        "compress_ms": last.get("compress_ms", 0.0),
                         "sweep_ms": last["sweep_ms"],
                         "sweep_gbs": last["sweep_bytes"] / max(last["sweep_ms"], 1e-9) / 1e6},
             "hodlr": {"tol": args.tol, "leaf": args.leaf, "compressed": bool(last["compressed"]),

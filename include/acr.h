@@ -164,6 +164,9 @@ typedef struct {
     long long gemm_launches, inv_launches, sweep_launches;
     long long launches_factor;           /* all kernel launches, last factor */
     long long launches_solve;            /* all kernel launches, last solve */
+    double compress_ms;                  /* HODLR compression of the last factor
+                                            (sketches, node SVDs, packing; 0 when
+                                            tol <= 0); included in factor_ms */
 } acr_stats_t;
 
 /* Copy the handle's statistics into *s. */

@@ -77,7 +77,7 @@ class acr_stats_t(ctypes.Structure):
                 ("sweep_ms", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
                 ("gemm_launches", ctypes.c_longlong), ("inv_launches", ctypes.c_longlong),
                 ("sweep_launches", ctypes.c_longlong), ("launches_factor", ctypes.c_longlong),
-                ("launches_solve", ctypes.c_longlong)]
+                ("launches_solve", ctypes.c_longlong), ("compress_ms", ctypes.c_double)]
 
 
 def load(path: str = LIB_PATH):

@@ -872,6 +872,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         float cms = 0.f;
         cudaEventElapsedTime(&cms, ce0, ce1);
         h->st.factor_ms += cms;
+        h->st.compress_ms = cms;
         h->st.launches_factor += launch_count() - c0;
     }
     return ACR_OK;

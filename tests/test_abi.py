@@ -90,3 +90,42 @@ def test_solve_bytes_bound(lib):
         lib.acr_solve_bytes(0, 64, 1, o)
     with pytest.raises(lib.AcrError):
         lib.acr_solve_bytes(64, 64, -1, o)
+
+
+_CTYPES = {"int": ctypes.c_int, "size_t": ctypes.c_size_t, "double": ctypes.c_double,
+           "long long": ctypes.c_longlong, "void *": ctypes.c_void_p}
+
+
+def _header_struct(name):
+    """(field, ctype) pairs of `typedef struct {...} name;` in include/acr.h."""
+    src = open(os.path.join(ROOT, "include", "acr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(long long|size_t|double|int|void)\s*(\*?)\s*(.*)", decl)
+        base = m.group(1) + (" *" if m.group(2) else "")
+        for var in m.group(3).split(","):
+            var = var.strip()
+            arr = re.match(r"(\w+)\[(\d+)\]", var)
+            if arr:
+                fields.append((arr.group(1), _CTYPES[base] * int(arr.group(2))))
+            else:
+                fields.append((var, _CTYPES[base]))
+    return fields
+
+
+@pytest.mark.parametrize("name", ["acr_opts", "acr_stats_t"])
+def test_binding_structs_match_header(name):
+    from paper_1604_00617_gb300 import _lib
+    want = _header_struct(name)
+    got = getattr(_lib, name)._fields_
+    assert [f for f, _ in got] == [f for f, _ in want]
+    for (f, tg), (_, tw) in zip(got, want):
+        if hasattr(tw, "_length_"):
+            assert tg._length_ == tw._length_ and tg._type_ is tw._type_, f
+        else:
+            assert tg is tw, f
