@@ -23,7 +23,9 @@
  *  - Right-hand sides B are N x nrhs column-major with leading dimension
  *    N = nblk*blksz, in natural block order.
  *  - Every pointer may be host or device memory; the library detects which
- *    (cudaPointerGetAttributes).  The caller keeps ownership of its buffers
+ *    (cudaPointerGetAttributes).  Device memory must belong to the handle's
+ *    device (the current device at acr_factor time); memory of another GPU is
+ *    rejected with ACR_ERR_INVALID_ARG.  The caller keeps ownership of its buffers
  *    and may free them as soon as the call returns; the library copies what
  *    it keeps.
  *  - Every call is synchronous with respect to the host: when it returns, the
@@ -195,9 +197,11 @@ const char *acr_last_error(void);
  *
  * Inverts, in place, `count` blocks of blksz x blksz (column-major, block
  * stride blksz*blksz) with the same partial-pivoting Gauss-Jordan kernels as
- * the factorization, in FP64.  mats and info are device memory owned by the
- * caller; info receives per block 0, or k+1 if pivot k was zero or not finite
- * (that block's contents are then meaningless).
+ * the factorization, in FP64.  mats and info are device memory of the
+ * current device, owned by the caller (host memory or memory of another GPU
+ * returns ACR_ERR_INVALID_ARG before anything is launched); info receives per
+ * block 0, or k+1 if pivot k was zero or not finite (that block's contents are
+ * then meaningless).
  *
  * Every temporary lives in one fixed scratch array of
  * ACR_NOALLOC_SCRATCH_BYTES compiled into the library, which each GPU that
@@ -212,7 +216,9 @@ const char *acr_last_error(void);
  * the GPU (different streams, or host threads racing) corrupt each other:
  * order them on one stream.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call outside any stream capture. */
+ * make that first call outside any stream capture.  The address is kept per
+ * device and CUDA context: after a device reset the next call looks it up
+ * again (make that call outside capture too). */
 #define ACR_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int acr_block_inverse_noalloc(int blksz, int count, double *mats, int *info, void *stream);
 

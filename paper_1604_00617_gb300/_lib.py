@@ -238,12 +238,16 @@ def acr_block_inverse_noalloc(blksz: int, count: int, mats, info, stream=None) -
     place on the device without allocating (``mats``: float64 device tensor,
     ``info``: int32 device tensor of ``count``).  Queued on ``stream`` (a CUDA
     stream handle or None); returns without waiting."""
-    if hasattr(info, "data_ptr"):
-        import torch
-        if info.dtype != torch.int32 or info.numel() < count:
-            raise TypeError("info must be an int32 tensor with count elements")
-        iptr = ctypes.c_void_p(info.data_ptr())
-    else:
-        raise TypeError("info must be a device tensor")
+    if not hasattr(info, "data_ptr") or not hasattr(mats, "data_ptr"):
+        raise TypeError("mats and info must be device tensors")
+    import torch
+    if info.dtype != torch.int32 or info.numel() < count:
+        raise TypeError("info must be an int32 tensor with count elements")
+    if not info.is_contiguous():
+        raise ValueError("info must be contiguous")
+    for name, t in (("mats", mats), ("info", info)):
+        if t.device.type != "cuda" or (torch.cuda.is_available() and t.device.index != torch.cuda.current_device()):
+            raise ValueError(f"{name} must be on the current CUDA device")
+    iptr = ctypes.c_void_p(info.data_ptr())
     _check(_lib.acr_block_inverse_noalloc(int(blksz), int(count), _ptr(mats, blksz * blksz * count), iptr,
                                           ctypes.c_void_p(stream) if stream else None))

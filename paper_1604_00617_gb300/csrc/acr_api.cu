@@ -74,15 +74,24 @@ int fail(int code, const char* fmt, ...) {
         }                                                                                 \
     } while (0)
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// Where a caller's buffer lives: host memory (pageable, pinned or unknown to
+// CUDA), device memory of the given device (or managed memory, reachable from
+// it), or device memory of another GPU.  Kernels here only dereference memory
+// of the handle's device: a buffer on another GPU is rejected before any
+// launch, since reading it without peer access would fault.
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+
+PtrKind ptr_kind(const void* p, int dev) {
+    if (!p) return PTR_HOST;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return PTR_HOST;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
+    return PTR_HOST;
 }
 
 struct Level {
@@ -544,9 +553,9 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     DevBuf sA, sD, sC;
     const double *dA = A, *dD = D, *dC = C;
     // A and C are never read when there is a single block
-    if (n > 1 && !is_device_ptr(A)) { CK(sA.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sA.p, A, nA * 8, cudaMemcpyHostToDevice, s)); dA = sA.as<double>(); }
-    if (!is_device_ptr(D)) { CK(sD.alloc(nD * 8, s)); CK(cudaMemcpyAsync(sD.p, D, nD * 8, cudaMemcpyHostToDevice, s)); dD = sD.as<double>(); }
-    if (n > 1 && !is_device_ptr(C)) { CK(sC.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sC.p, C, nA * 8, cudaMemcpyHostToDevice, s)); dC = sC.as<double>(); }
+    if (n > 1 && ptr_kind(A, h->dev) != PTR_DEVICE) { CK(sA.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sA.p, A, nA * 8, cudaMemcpyHostToDevice, s)); dA = sA.as<double>(); }
+    if (ptr_kind(D, h->dev) != PTR_DEVICE) { CK(sD.alloc(nD * 8, s)); CK(cudaMemcpyAsync(sD.p, D, nD * 8, cudaMemcpyHostToDevice, s)); dD = sD.as<double>(); }
+    if (n > 1 && ptr_kind(C, h->dev) != PTR_DEVICE) { CK(sC.alloc(nA * 8, s)); CK(cudaMemcpyAsync(sC.p, C, nA * 8, cudaMemcpyHostToDevice, s)); dC = sC.as<double>(); }
     if (n == 1) { dA = nullptr; dC = nullptr; }
 
     // ---- FP64 operator copy (residual of the refinement) -----------------
@@ -1565,7 +1574,7 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
     const long long N = (long long)n * b;
     cudaStream_t s = h->stream;
     const size_t bytes = (size_t)N * nrhs * 8;
-    const bool dev = is_device_ptr(B);
+    const bool dev = ptr_kind(B, h->dev) == PTR_DEVICE;
     DevBuf dB;
     double* f = B;
     Events evown;
@@ -1712,6 +1721,16 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     if (op.m_stop > 1) return fail(ACR_ERR_INVALID_ARG, "m_stop > 1 is not supported (reduction runs to one block)");
     if (op.ir_max_iter <= 0) op.ir_max_iter = 20;
     if (!(op.ir_tol > 0)) op.ir_tol = 1e-8;
+    {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaGetLastError();
+        const double* arr[3] = {A, D, C};
+        const char* nm[3] = {"A", "D", "C"};
+        for (int q = 0; q < 3; ++q)
+            if ((q == 1 || nblk > 1) && ptr_kind(arr[q], cur) == PTR_OTHER_DEVICE)
+                return fail(ACR_ERR_INVALID_ARG, "%s is device memory of another GPU than the current device %d", nm[q], cur);
+    }
     acr_ctx* h = new (std::nothrow) acr_ctx();
     if (!h) return fail(ACR_ERR_OOM, "host allocation failed");
     h->n = nblk; h->b = blksz; h->prec = op.precision; h->in_kind = op.input_kind; h->tol = tol; h->opts = op;
@@ -1755,6 +1774,8 @@ int acr_solve_ex(acr_handle h, double* B, int nrhs, double* resid_out, int* iter
     if (nrhs < 0 || (nrhs > 0 && !B)) return fail(ACR_ERR_INVALID_ARG, "bad right-hand side");
     if (iters_out) *iters_out = 0;
     if (nrhs == 0) return ACR_OK;
+    if (ptr_kind(B, h->dev) == PTR_OTHER_DEVICE)
+        return fail(ACR_ERR_INVALID_ARG, "B is device memory of another GPU than the handle's device %d", h->dev);
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != h->dev) cudaSetDevice(h->dev);

@@ -12,8 +12,11 @@
 // The scratch is a file-scope __device__ array of ACR_NOALLOC_SCRATCH_BYTES
 // (16 MiB).  Every GPU on which the library's module is loaded holds it until
 // the process exits.  In host code the array's name is only a host-side
-// stand-in, so its device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// stand-in, so its device address is looked up with cudaGetSymbolAddress,
+// with the device current, and cached per device together with the identity
+// of the CUDA context it belongs to.  A device reset destroys that context
+// (and the module with the array); the next call sees a different context and
+// looks the address up again instead of using the stale one.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -30,6 +33,34 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// cuCtxGetCurrent and cuCtxGetId); 0 if there is none or it cannot be read.
+unsigned long long current_context_id() {
+    typedef int (*GetCurrent)(void**);
+    typedef int (*GetId)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int err(int code, const char* fmt, long long a = 0, long long b = 0, long long c = 0) {
     char buf[256];
@@ -37,13 +68,16 @@ int err(int code, const char* fmt, long long a = 0, long long b = 0, long long c
     return acr::set_last_error(code, buf);
 }
 
-bool on_device(const void* p) {
+// Device memory of GPU `dev` (or managed memory).  Memory of another GPU is
+// refused: the kernels run on the current device and would fault reading it.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -52,8 +86,6 @@ extern "C" int acr_block_inverse_noalloc(int blksz, int count, double* mats, int
     if (blksz < 1 || count < 0) return err(ACR_ERR_INVALID_ARG, "blksz must be >= 1 and count >= 0 (got %lld, %lld)", blksz, count);
     if (count == 0) return ACR_OK;
     if (!mats || !info) return err(ACR_ERR_INVALID_ARG, "mats and info must not be NULL");
-    if (!on_device(mats) || !on_device(info))
-        return err(ACR_ERR_INVALID_ARG, "mats and info must be device memory");
     const size_t need = acr::gj_scratch_bytes<double>(blksz, count);
     if (need > kScratchBytes)
         return err(ACR_ERR_INVALID_ARG,
@@ -62,14 +94,18 @@ extern "C" int acr_block_inverse_noalloc(int blksz, int count, double* mats, int
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
-        return err(ACR_ERR_CUDA, "no usable current device (%lld)", dev);
+        return err(ACR_ERR_INVALID_ARG, "no usable current CUDA device (%lld)", dev);
     }
+    if (!on_device(mats, dev) || !on_device(info, dev))
+        return err(ACR_ERR_INVALID_ARG, "mats and info must be device memory of the current device %lld", dev);
     void* scratch = nullptr;
     {
-        // first call on this device: look up the array's device address with
-        // this device current (not capturable: make this call before capture)
+        // first call on this device (or in a new context after a device
+        // reset): look up the array's device address with this device
+        // current (not capturable: make this call before any capture)
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -77,6 +113,7 @@ extern "C" int acr_block_inverse_noalloc(int blksz, int count, double* mats, int
                 return err(ACR_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed (error %lld)", (long long)e);
             }
             g_scratch_addr[dev] = p;
+            g_scratch_ctx[dev] = current_context_id();
         }
         scratch = g_scratch_addr[dev];
     }

@@ -129,3 +129,19 @@ def test_binding_structs_match_header(name):
             assert tg._length_ == tw._length_ and tg._type_ is tw._type_, f
         else:
             assert tg is tw, f
+
+
+def test_noalloc_rejects_host_memory_without_launching(lib):
+    """acr_block_inverse_noalloc accepts only device memory of the current
+    device; host buffers are refused before anything is queued (on a machine
+    without a GPU the call fails the same way, with no current device)."""
+    import numpy as np
+    mats = np.eye(4).ravel().copy()
+    info = np.zeros(1, dtype=np.int32)
+    code = lib._lib.acr_block_inverse_noalloc(4, 1, ctypes.c_void_p(mats.ctypes.data),
+                                              ctypes.c_void_p(info.ctypes.data), None)
+    assert code == lib.ACR_ERR_INVALID_ARG
+    assert "device" in lib.acr_last_error()
+    assert (mats == np.eye(4).ravel()).all() and info[0] == 0
+    with pytest.raises(TypeError):
+        lib.acr_block_inverse_noalloc(4, 1, mats, info)

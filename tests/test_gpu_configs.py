@@ -1,0 +1,149 @@
+"""The workloads at their full sizes and settings, compressed, through the C ABI.
+
+* Helmholtz 1024^2 (N = 1,048,576) exactly as the benchmark times it: HODLR
+  tol 1e-8, leaf 64, FP32 tensor-core factor, FP64 FGMRES to 1e-8 per column;
+  the residual of every column is recomputed on the host (numpy banded
+  product), and the reported ranks per level are checked for consistency.
+  The same system with the FP64 factor (the comparator of the benchmark).
+* Variable-coefficient diffusion 256^2 (256 blocks of 256 x 256), tol 1e-6,
+  leaf 32, 16 right-hand sides: FP64 without refinement meets the stated
+  compressed bound (relative residual <= 10 tol) and is compared with the
+  FP64 oracle; the FP32 tensor-core factor refines to 1e-8 and is compared
+  with the oracle too.
+* Convection-diffusion 512^2, tol 1e-6, leaf 64, 64 right-hand sides, FP32
+  tensor-core factor refined to 1e-8.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1604_00617_gb300 import build
+    build()
+    from paper_1604_00617_gb300 import _lib
+    return _lib
+
+
+def factor(lib, P, tol, prec, **kw):
+    a, D3, c = P.banded_abi()
+    o = lib.acr_default_opts()
+    o.precision = prec
+    o.input_kind = lib.ACR_BANDED
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return lib.acr_factor_ex(P.nblk, P.b, a, D3, c, tol, o)
+
+
+def solve(lib, h, F):
+    B = np.asfortranarray(F.copy())
+    res, it = lib.acr_solve_ex(h, B, F.shape[1])
+    return B, res, it
+
+
+def host_resid(P, X, F):
+    return np.linalg.norm(F - P.matvec(X), axis=0) / np.linalg.norm(F, axis=0)
+
+
+def relerr(x, y):
+    return np.linalg.norm(x - y) / np.linalg.norm(y)
+
+
+def _check_ranks(s, b, leaf):
+    """Ranks per level: level 0 (inverses of tridiagonal blocks) is rank 1,
+    every level's mean is at most its maximum, and no rank exceeds the largest
+    node (b / 2 rows)."""
+    assert s["compressed"] == 1
+    assert s["rank_max"][0] == 1
+    for mx, mean in zip(s["rank_max"], s["rank_mean"]):
+        assert 0 <= mean <= mx <= b // 2, (s["rank_max"], s["rank_mean"])
+
+
+def test_bench_configuration_helmholtz_1m(lib):
+    P = syn.make_config(3)
+    F = syn.rhs_uniform(P.N, 8, 2003)
+    h = factor(lib, P, 1e-8, lib.ACR_FP32TC_IR, leaf=64, ir_tol=1e-8, ir_max_iter=60)
+    try:
+        s = lib.acr_stats(h)
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert s["levels"] == 11
+    _check_ranks(s, P.b, 64)
+    assert (res <= 1e-8).all(), (res, it)
+    assert (host_resid(P, X, F) <= 1.5e-8).all()
+    print(f"helmholtz1024 tol 1e-8 fp32tc: {it} preconditioner solves, ranks {s['rank_max']}")
+
+
+def test_fp64_comparator_helmholtz_1m(lib):
+    P = syn.make_config(3)
+    F = syn.rhs_uniform(P.N, 8, 2003)
+    h = factor(lib, P, 1e-8, lib.ACR_FP64, leaf=64, ir_tol=1e-8, ir_max_iter=60)
+    try:
+        s = lib.acr_stats(h)
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    _check_ranks(s, P.b, 64)
+    assert (res <= 1e-8).all(), (res, it)
+    assert (host_resid(P, X, F) <= 1.5e-8).all()
+
+
+@pytest.fixture(scope="module")
+def diffusion256():
+    P = syn.make_config(1)
+    F = syn.rhs_uniform(P.N, 16, 2001)
+    A, D, C = P.dense_blocks()
+    return P, F, oracle.bcr_solve(A, D, C, F)
+
+
+def test_diffusion256_fp64_compressed_within_10_tol(lib, diffusion256):
+    P, F, Xo = diffusion256
+    tol = 1e-6
+    h = factor(lib, P, tol, lib.ACR_FP64, leaf=32, refine=lib.ACR_REFINE_NONE, ir_tol=10 * tol)
+    try:
+        s = lib.acr_stats(h)
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    _check_ranks(s, P.b, 32)
+    assert (res <= 10 * tol).all(), res
+    assert (host_resid(P, X, F) <= 10 * tol * 1.01).all()
+    # error against the FP64 oracle, per column, bounded by the conditioning
+    err = np.linalg.norm(X - Xo, axis=0) / np.linalg.norm(Xo, axis=0)
+    assert (err <= 1e4 * tol).all(), err
+    print(f"diffusion256 fp64 tol 1e-6: resid max {res.max():.2e}, error vs oracle max {err.max():.2e}")
+
+
+def test_diffusion256_fp32tc_compressed_refined(lib, diffusion256):
+    P, F, Xo = diffusion256
+    h = factor(lib, P, 1e-6, lib.ACR_FP32TC_IR, leaf=32, ir_max_iter=60)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all(), (res, it)
+    assert (host_resid(P, X, F) <= 1.5e-8).all()
+    err = np.linalg.norm(X - Xo, axis=0) / np.linalg.norm(Xo, axis=0)
+    assert (err <= 1e-4).all(), err
+    print(f"diffusion256 fp32tc tol 1e-6: {it} solves, error vs oracle max {err.max():.2e}")
+
+
+def test_convdiff512_fp32tc_compressed_refined(lib):
+    P = syn.make_config(2)
+    F = syn.rhs_uniform(P.N, 64, 2002)
+    h = factor(lib, P, 1e-6, lib.ACR_FP32TC_IR, leaf=64, ir_max_iter=60)
+    try:
+        s = lib.acr_stats(h)
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    _check_ranks(s, P.b, 64)
+    assert (res <= 1e-8).all(), (res, it)
+    assert (host_resid(P, X, F) <= 1.5e-8).all()

@@ -42,14 +42,14 @@ def factor(lib, A, D, C, prec=0, device=False, **kw):
     return lib.acr_factor_ex(n, b, Ac, Dc, Cc, 0.0, o)
 
 
-def factor_banded(lib, P, prec=0, **kw):
+def factor_banded(lib, P, prec=0, tol=0.0, **kw):
     a, D3, c = P.banded_abi()
     o = lib.acr_default_opts()
     o.precision = prec
     o.input_kind = lib.ACR_BANDED
     for k, v in kw.items():
         setattr(o, k, v)
-    return lib.acr_factor_ex(P.nblk, P.b, a, D3, c, 0.0, o)
+    return lib.acr_factor_ex(P.nblk, P.b, a, D3, c, tol, o)
 
 
 def solve(lib, h, F, device=False):

@@ -319,3 +319,38 @@ def test_pins_catch_planted_mistakes(mutant):
     finally:
         oracle.use_mutant(0)
     assert max(errs) > 1e-6, errs
+
+
+# ------------------------------------------------ residual and early stop pins
+
+@pytest.mark.parametrize("n,b,seed", [(1, 5, 1), (4, 3, 2), (7, 6, 3), (12, 9, 4)])
+def test_oracle_residual_against_assembled_matrix(n, b, seed):
+    """``oracle.residual`` is ||F - M X||_2 / ||F||_2 per column; recomputed
+    here with the assembled matrix and numpy, for arbitrary X (not a
+    solution), and ~0 for the brute-force solution."""
+    A, D, C = syn.random_blocks(n, b, seed)
+    rng = np.random.default_rng(seed + 3)
+    F = rng.standard_normal((n * b, 3))
+    X = rng.standard_normal((n * b, 3))
+    M = _assemble(A, D, C)
+    want = np.linalg.norm(F - M @ X, axis=0) / np.linalg.norm(F, axis=0)
+    got = oracle.residual(A, D, C, X, F)
+    assert np.allclose(got, want, rtol=1e-12, atol=0), (got, want)
+    Xs = np.linalg.solve(M, F)
+    assert (oracle.residual(A, D, C, Xs, F) <= 1e-13).all()
+
+
+@pytest.mark.parametrize("n,m_stop", [(8, 2), (8, 3), (11, 2), (11, 5), (16, 4), (9, 9), (6, 20)])
+def test_early_stop_top_solve_brute_force(n, m_stop):
+    """Section 3 allows the reduction to stop once the system is small
+    enough; the remaining m <= m_stop blocks are then solved as one dense
+    system.  Every stopping point gives the brute-force solution."""
+    b = 5
+    A, D, C = syn.random_blocks(n, b, seed=n + 17 * m_stop)
+    F = np.random.default_rng(m_stop).standard_normal((n * b, 2))
+    X = oracle.bcr_solve(A, D, C, F, m_stop=m_stop)
+    assert _rel(X, np.linalg.solve(_assemble(A, D, C), F)) <= 1e-12
+    # the schedule: the last entry lists the blocks of the top solve
+    sched = oracle.bcr_schedule(n, m_stop)
+    assert 1 <= len(sched[-1]) <= max(1, m_stop)
+    assert sorted(i for lv in sched for i in lv) == list(range(n))
