@@ -53,6 +53,8 @@ def parse():
                         "blocks at the first level)")
     p.add_argument("--tol", type=float, default=1e-8, help="HODLR compression tolerance (0: dense blocks)")
     p.add_argument("--leaf", type=int, default=64, help="HODLR leaf size")
+    p.add_argument("--h-levels", type=int, default=0,
+                   help="reduction levels in HODLR arithmetic (0: automatic, -1: none)")
     p.add_argument("--no-dense", action="store_true", help="skip the dense-block (tol 0) comparison")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving mix (0: skip)")
     p.add_argument("--serving-rate", type=float, default=200.0, help="offered rate of the serving mix, req/s")
@@ -328,6 +330,7 @@ def run_ours(args):
         o.ir_tol = 1e-8
         o.ir_max_iter = 60
         o.leaf = args.leaf
+        o.h_levels = args.h_levels
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         return o
 

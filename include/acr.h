@@ -92,7 +92,24 @@ typedef struct {
                            the factorization's memory is allocated and freed
                            in stream order on it); NULL: a library stream */
     int refine;         /* enum acr_refine, default ACR_REFINE_FGMRES */
+    int h_levels;       /* tol > 0 with ACR_BANDED input: reduction levels carried
+                           out in HODLR arithmetic (Section 3: H-inverse of the
+                           eliminated blocks, H-products and H-sums truncated to
+                           tol / 10), the remaining levels with dense blocks
+                           compressed afterwards.  0 (default): from level 0 on, as long as
+                           the ranks stay small (at most ACR_HRANK_SWITCH);
+                           k > 0: at most k levels; -1: none (every level dense,
+                           compressed after the reduction) */
 } acr_opts;
+
+/* Largest off-diagonal rank of a level's blocks for which the automatic
+ * choice (h_levels = 0) continues in HODLR arithmetic.  A level also goes
+ * dense when its HODLR inverses miss the identity on random vectors by more
+ * than 1e3 times the truncation tolerance (see h_check in acr_stats_t).  The
+ * HODLR arithmetic truncates at max(tol / 10, a few units of the factor's
+ * rounding), so that the truncations accumulated over the levels keep the
+ * solve near tol. */
+#define ACR_HRANK_SWITCH 32
 
 #define ACR_FGMRES_RESTART 50
 
@@ -169,6 +186,13 @@ typedef struct {
     double compress_ms;                  /* HODLR compression of the last factor
                                             (sketches, node SVDs, packing; 0 when
                                             tol <= 0); included in factor_ms */
+    int h_levels;                        /* levels reduced in HODLR arithmetic */
+    double h_ms;                         /* their device time (included in factor_ms) */
+    double h_flops;                      /* algorithmic flops of their products */
+    double h_host_ms;                    /* host time spent building their launches */
+    double h_check[32];                  /* per level reduced in HODLR arithmetic (and the
+                                            first level that failed it): the inverse check
+                                            max_j ||D_j (D_j^-1 x) - x|| / ||x|| on random x */
 } acr_stats_t;
 
 /* Copy the handle's statistics into *s. */

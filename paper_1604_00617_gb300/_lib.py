@@ -39,6 +39,9 @@ ACR_REFINE_FGMRES = 0
 ACR_REFINE_IR = 1
 ACR_REFINE_NONE = 2
 
+# largest rank for which the automatic choice continues in HODLR arithmetic
+ACR_HRANK_SWITCH = 32
+
 _NAMES = {0: "ACR_OK", -1: "ACR_ERR_INVALID_ARG", -2: "ACR_ERR_OOM", -3: "ACR_ERR_SINGULAR",
           -4: "ACR_ERR_NOT_CONVERGED", -5: "ACR_ERR_CUDA", -6: "ACR_ERR_TIMEOUT"}
 
@@ -61,7 +64,8 @@ class AcrError(RuntimeError):
 class acr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("input_kind", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("m_stop", ctypes.c_int), ("ir_tol", ctypes.c_double),
-                ("ir_max_iter", ctypes.c_int), ("stream", ctypes.c_void_p), ("refine", ctypes.c_int)]
+                ("ir_max_iter", ctypes.c_int), ("stream", ctypes.c_void_p), ("refine", ctypes.c_int),
+                ("h_levels", ctypes.c_int)]
 
 
 class acr_stats_t(ctypes.Structure):
@@ -77,7 +81,9 @@ class acr_stats_t(ctypes.Structure):
                 ("sweep_ms", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
                 ("gemm_launches", ctypes.c_longlong), ("inv_launches", ctypes.c_longlong),
                 ("sweep_launches", ctypes.c_longlong), ("launches_factor", ctypes.c_longlong),
-                ("launches_solve", ctypes.c_longlong), ("compress_ms", ctypes.c_double)]
+                ("launches_solve", ctypes.c_longlong), ("compress_ms", ctypes.c_double),
+                ("h_levels", ctypes.c_int), ("h_ms", ctypes.c_double), ("h_flops", ctypes.c_double),
+                ("h_host_ms", ctypes.c_double), ("h_check", ctypes.c_double * 32)]
 
 
 def load(path: str = LIB_PATH):
@@ -216,6 +222,7 @@ def acr_stats(h) -> dict:
     d = {k: getattr(s, k) for k, _ in acr_stats_t._fields_}
     d["rank_max"] = list(s.rank_max)[: s.levels]
     d["rank_mean"] = list(s.rank_mean)[: s.levels]
+    d["h_check"] = list(s.h_check)[: min(32, s.h_levels + 1)]
     return d
 
 

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -37,6 +38,7 @@
 
 #include "../../include/acr.h"
 #include "acr_internal.h"
+#include "hred.cuh"
 
 using namespace acr;
 
@@ -198,13 +200,15 @@ void default_opts(acr_opts* o) {
     o->ir_max_iter = 20;
     o->stream = nullptr;
     o->refine = ACR_REFINE_FGMRES;
+    o->h_levels = 0;
 }
 
 // Level plan and persistent byte offsets.  Returns the arena size.  With
 // band0 (5-point operator, level-0 A_i and C_i diagonal) level 0 keeps only
 // the diagonals: xa/xc hold a_j, c_j of the eliminated blocks (b values each;
 // D_j^-1 A_j is applied as D_j^-1 (a_j .* u)) and ak/ck those of the kept ones.
-size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev, bool band0 = false) {
+// Levels below t0 are reduced in HODLR arithmetic and take no dense storage.
+size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev, bool band0 = false, int t0 = 0) {
     lev.clear();
     const size_t blk = (size_t)b * b * es;
     size_t off = 0;
@@ -215,8 +219,10 @@ size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev, bool band0 
         L.ne = (m + 1) / 2;
         L.nk = m / 2;
         const bool top = (m == 1);
-        const size_t ob = (band0 && m == n) ? (size_t)b * es : blk;  // off-diagonal storage per block
-        L.off_dinv = off; off += L.ne * blk;
+        const bool none = (int)lev.size() < t0;
+        const size_t ob = none ? 0 : ((band0 && m == n) ? (size_t)b * es : blk);  // off-diagonal storage per block
+        const size_t db = none ? 0 : blk;
+        L.off_dinv = off; off += L.ne * db;
         L.off_xa = off; off += top ? 0 : L.ne * ob;
         L.off_xc = off; off += top ? 0 : L.ne * ob;
         L.off_ak = off; off += L.nk * ob;
@@ -227,6 +233,15 @@ size_t plan_levels(int n, int b, size_t es, std::vector<Level>& lev, bool band0 
         m = m / 2;
     }
     return off;
+}
+
+// HODLR tree of a b x b block for a requested leaf size: the largest depth L
+// with b divisible by 2^L and leaves b / 2^L no smaller than the request.
+void hodlr_tree(int b, int want_leaf, int& L, int& leaf) {
+    const int want = std::max(1, want_leaf);
+    L = 0;
+    while ((b % (2 << L)) == 0 && (b >> (L + 1)) >= want && L < hred::HMAXL_TREE) ++L;
+    leaf = b >> L;
 }
 
 // Algorithmic flops of block cyclic reduction from level t0 on: 2 b^3 per
@@ -269,25 +284,33 @@ int default_leaf(int b) {
 }
 
 template <class T>
-int compress_factor(acr_ctx* h) {
+int compress_factor(acr_ctx* h, hred::Result<T>* hres = nullptr) {
     const int b = h->b;
     const size_t bb = h->bb();
     cudaStream_t s = h->stream;
     // tree depth: the largest L with b divisible by 2^L and leaves b / 2^L no
     // smaller than the requested leaf size
-    const int want = std::max(1, h->opts.leaf > 0 ? h->opts.leaf : default_leaf(b));
-    int L = 0;
-    while ((b % (2 << L)) == 0 && (b >> (L + 1)) >= want) ++L;
-    const int leaf = b >> L;
+    int L = 0, leaf = b;
+    hodlr_tree(b, h->opts.leaf > 0 ? h->opts.leaf : default_leaf(b), L, leaf);
     h->leaf = leaf;
     h->hL = L;
     const int max_rank = h->opts.max_rank > 0 ? h->opts.max_rank : 0;
     const int kmax = max_rank > 0 ? std::min(64, std::max(16, ((max_rank + 8) + 1) / 2 * 2)) : 32;
     const double tol = h->tol_eff;
     const int T_ = h->levels() - 1;
+    const int th = hres ? hres->th : 0;  // levels below th were reduced in HODLR arithmetic
 
     // ---- the stored blocks -----------------------------------------------------
+    // Global block ids: first the blocks of the HODLR-arithmetic levels
+    // (already compressed, ids < NW), then the dense blocks of the later levels
+    // (compressed here by sketching; dense index = id - NW).
+    struct WEnt {
+        const hred::HSet<T>* set;
+        int idx;
+    };
+    std::vector<WEnt> went;
     std::vector<const T*> blocks;
+    int nid = 0;
     h->bid.assign(T_ + 1, std::vector<std::vector<int>>(5));
     for (int t = 0; t <= T_; ++t) {
         const Level& Lv = h->lev[t];
@@ -296,10 +319,28 @@ int compress_factor(acr_ctx* h) {
             h->bid[t][arr].assign(count, -1);
             for (int e = 0; e < count; ++e)
                 if (used(e)) {
-                    h->bid[t][arr][e] = (int)blocks.size();
+                    h->bid[t][arr][e] = nid++;
                     blocks.push_back(h->P<T>(off) + (size_t)e * bb);
                 }
         };
+        auto addw = [&](int arr, const hred::HSet<T>* set, int count, auto idx, auto used) {
+            h->bid[t][arr].assign(count, -1);
+            for (int e = 0; e < count; ++e)
+                if (used(e)) {
+                    h->bid[t][arr][e] = nid++;
+                    went.push_back({set, idx(e)});
+                }
+        };
+        if (t < th) {
+            addw(0, hres->dinv[t].get(), Lv.ne, [](int e) { return e; }, [](int) { return true; });
+            if (t == T_ || diag0) continue;
+            addw(1, hres->x[t].get(), Lv.ne, [](int e) { return 2 * e; }, [](int e) { return 2 * e > 0; });
+            addw(2, hres->x[t].get(), Lv.ne, [](int e) { return 2 * e + 1; }, [&](int e) { return 2 * e + 1 < Lv.m; });
+            addw(3, hres->ac[t].get(), Lv.nk, [](int k) { return 2 * (2 * k + 1); }, [](int) { return true; });
+            addw(4, hres->ac[t].get(), Lv.nk, [](int k) { return 2 * (2 * k + 1) + 1; },
+                 [&](int k) { return 2 * k + 2 < Lv.m; });
+            continue;
+        }
         add(0, Lv.off_dinv, Lv.ne, [](int) { return true; });
         if (t == T_ || diag0) continue;
         add(1, Lv.off_xa, Lv.ne, [](int e) { return 2 * e > 0; });
@@ -307,10 +348,12 @@ int compress_factor(acr_ctx* h) {
         add(3, Lv.off_ak, Lv.nk, [](int) { return true; });
         add(4, Lv.off_ck, Lv.nk, [&](int k) { return 2 * k + 2 < Lv.m; });
     }
-    const int NB = (int)blocks.size();
+    const int NW = (int)went.size();
+    const int NBd = (int)blocks.size();
+    const int NB = NW + NBd;
     const int npb = (1 << (L + 1)) - 2;  // off-diagonal nodes per block
 
-    // ---- sketch, QR + SVD, V for every tree level ------------------------------
+    // ---- sketch, QR + SVD, V for every tree level (dense blocks) ---------------
     // Two passes per tree level: every node is sketched with k1 = 16 columns
     // (ranks at most k1 - 4 are resolved by it); only the nodes whose sketch
     // saturates are sketched again with k = kmax.  Most nodes of the low
@@ -375,8 +418,8 @@ int compress_factor(acr_ctx* h) {
             while (r < k && (double)sg[r] > tol * (double)sg[0]) ++r;
         return r;
     };
-    for (int l = 1; l <= L; ++l) {
-        const int sz = b >> l, nn = NB << l;
+    for (int l = 1; l <= L && NBd > 0; ++l) {
+        const int sz = b >> l, nn = NBd << l;
         int kbig = std::min(kmax, sz);
         kbig -= kbig & 1;
         if (kbig < 2) kbig = 2;
@@ -423,14 +466,20 @@ int compress_factor(acr_ctx* h) {
         const int sz = b >> l;
         for (int g = 0; g < NB; ++g)
             for (int ni = 0; ni < (1 << l); ++ni) {
-                const size_t id = ((size_t)g << l) + ni;
-                const int sp = sat_pos[l][id];
-                const int k = sp >= 0 ? kl2[l] : kl[l];
-                const T* sg = sp >= 0 ? hsig2[l].data() + (size_t)sp * k : hsig[l].data() + id * k;
-                int r = rank_of(sg, k);
-                if (max_rank > 0 && r > max_rank) r = max_rank;
-                const bool sketch_full = (k < sz) && (r > k - 4);
-                const bool dense = sketch_full || (2 * r >= sz);
+                int r = 0;
+                bool dense = false;
+                if (g < NW) {
+                    r = went[g].set->rk(went[g].idx, l, ni);
+                } else {
+                    const size_t id = ((size_t)(g - NW) << l) + ni;
+                    const int sp = sat_pos[l][id];
+                    const int k = sp >= 0 ? kl2[l] : kl[l];
+                    const T* sg = sp >= 0 ? hsig2[l].data() + (size_t)sp * k : hsig[l].data() + id * k;
+                    r = rank_of(sg, k);
+                    if (max_rank > 0 && r > max_rank) r = max_rank;
+                    const bool sketch_full = (k < sz) && (r > k - 4);
+                    dense = sketch_full || (2 * r >= sz);
+                }
                 HNode& hn = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
                 hn.pad = 0;
                 hn.off = off;
@@ -457,29 +506,76 @@ int compress_factor(acr_ctx* h) {
     CK(cudaMemcpyAsync(h->hblks.p, hb.data(), (size_t)NB * sizeof(HBlk), cudaMemcpyHostToDevice, s));
 
     // ---- pack ----------------------------------------------------------------------
-    {
-        std::vector<long long> lo(NB);
-        for (int g = 0; g < NB; ++g) lo[g] = hb[g].leaf_off;
+    if (NW > 0) {
+        // blocks of the HODLR-arithmetic levels: leaves as they are, nodes at
+        // their kept ranks (U, then V^T)
+        std::vector<CProb<T>> cp;
+        std::vector<PProb<T>> pp;
+        const size_t bl = (size_t)b * leaf;
+        for (int g = 0; g < NW; ++g) {
+            CProb<T> c;
+            memset(&c, 0, sizeof(c));
+            c.src = went[g].set->lf(went[g].idx, 0);
+            c.dst = h->hpool.as<T>() + hb[g].leaf_off;
+            c.lds = c.ldd = (int)bl;
+            c.rows = (int)bl;
+            c.cols = 1;
+            c.alpha = T(1);
+            cp.push_back(c);
+            for (int l = 1; l <= L; ++l) {
+                const int sz = b >> l;
+                for (int ni = 0; ni < (1 << l); ++ni) {
+                    const HNode& hn = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
+                    if (hn.rank <= 0) continue;
+                    PProb<T> q;
+                    q.U = went[g].set->Up(went[g].idx, l) + (size_t)ni * sz;
+                    q.V = went[g].set->Vp(went[g].idx, l) + (size_t)(ni ^ 1) * sz;
+                    q.dst = h->hpool.as<T>() + hn.off;
+                    q.ldu = q.ldv = b;
+                    q.s = sz;
+                    q.rank = hn.rank;
+                    pp.push_back(q);
+                }
+            }
+        }
+        std::vector<int2> ch;
+        for (size_t i = 0; i < cp.size(); ++i) hcopy_chunks((int)i, (long long)bl, ch);
+        DevBuf dcp, dch, dpp;
+        CK(dcp.alloc(cp.size() * sizeof(CProb<T>), s));
+        CK(dch.alloc(ch.size() * sizeof(int2), s));
+        CK(cudaMemcpyAsync(dcp.p, cp.data(), cp.size() * sizeof(CProb<T>), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dch.p, ch.data(), ch.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        CK(hcopy<T>(dcp.as<CProb<T>>(), dch.as<int2>(), (long long)ch.size(), s));
+        if (!pp.empty()) {
+            CK(dpp.alloc(pp.size() * sizeof(PProb<T>), s));
+            CK(cudaMemcpyAsync(dpp.p, pp.data(), pp.size() * sizeof(PProb<T>), cudaMemcpyHostToDevice, s));
+            CK(hpack<T>(dpp.as<PProb<T>>(), (int)pp.size(), s));
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+    if (NBd > 0) {
+        std::vector<long long> lo(NBd);
+        for (int d = 0; d < NBd; ++d) lo[d] = hb[NW + d].leaf_off;
         DevBuf dblk, dlo;
-        CK(dblk.alloc((size_t)NB * sizeof(void*), s));
-        CK(dlo.alloc((size_t)NB * sizeof(long long), s));
-        CK(cudaMemcpyAsync(dblk.p, blocks.data(), (size_t)NB * sizeof(void*), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(dlo.p, lo.data(), (size_t)NB * sizeof(long long), cudaMemcpyHostToDevice, s));
-        CK(pack_leaves<T>(dblk.as<const T*>(), dlo.as<long long>(), NB, b, leaf, h->hpool.as<T>(), s));
+        CK(dblk.alloc((size_t)NBd * sizeof(void*), s));
+        CK(dlo.alloc((size_t)NBd * sizeof(long long), s));
+        CK(cudaMemcpyAsync(dblk.p, blocks.data(), (size_t)NBd * sizeof(void*), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dlo.p, lo.data(), (size_t)NBd * sizeof(long long), cudaMemcpyHostToDevice, s));
+        CK(pack_leaves<T>(dblk.as<const T*>(), dlo.as<long long>(), NBd, b, leaf, h->hpool.as<T>(), s));
         for (int l = 1; l <= L; ++l) {
-            const int sz = b >> l, nn = NB << l, ns = (int)sat[l].size();
+            const int sz = b >> l, nn = NBd << l, ns = (int)sat[l].size();
             // first launch: every node, the second-pass ones marked to skip
             // (rank -2); second launch: the second-pass nodes
             std::vector<HNode> lv((size_t)nn + ns);
             std::vector<const T*> src((size_t)nn + ns);
-            for (int g = 0; g < NB; ++g)
+            for (int d = 0; d < NBd; ++d)
                 for (int ni = 0; ni < (1 << l); ++ni) {
-                    const size_t id = ((size_t)g << l) + ni;
-                    const HNode hn = nodes[(size_t)g * npb + ((1 << l) - 2) + ni];
+                    const size_t id = ((size_t)d << l) + ni;
+                    const HNode hn = nodes[(size_t)(NW + d) * npb + ((1 << l) - 2) + ni];
                     const int p = ni >> 1, lower = ni & 1;
                     const int r0 = lower ? (2 * p + 1) * sz : 2 * p * sz;
                     const int c0 = lower ? 2 * p * sz : (2 * p + 1) * sz;
-                    const T* B = blocks[g] + r0 + (size_t)c0 * b;
+                    const T* B = blocks[d] + r0 + (size_t)c0 * b;
                     const int sp = sat_pos[l][id];
                     lv[id] = hn;
                     src[id] = B;
@@ -504,7 +600,9 @@ int compress_factor(acr_ctx* h) {
         CK(cudaStreamSynchronize(s));
     }
     // ---- keep the level-0 diagonals, release the dense arena ------------------------
-    if (h->band0 && T_ > 0) {
+    // (with level 0 reduced in HODLR arithmetic they were staged into hdiag
+    // before the reduction)
+    if (h->band0 && T_ > 0 && th == 0) {
         const Level& L0 = h->lev[0];
         const size_t n4[4] = {(size_t)L0.ne * b, (size_t)L0.ne * b, (size_t)L0.nk * b, (size_t)L0.nk * b};
         const size_t src4[4] = {L0.off_xa, L0.off_xc, L0.off_ak, L0.off_ck};
@@ -605,18 +703,123 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
             }
         h->band0 = dom;
     }
+
+    // ---- the low levels in HODLR arithmetic (tol > 0, 5-point operator) -----
+    // Level 0 starts from the exact HODLR form of the input (tridiagonal D_i:
+    // rank 1; diagonal A_i, C_i), and the reduction goes on in H-arithmetic
+    // while the ranks stay small; the levels from th on are reduced with dense
+    // blocks and compressed afterwards.
+    // (declared in this order so that the block sets in hres, whose buffers
+    // unregister themselves from hr's range set, are released first)
+    std::unique_ptr<hred::Red<T>> hr;
+    hred::Result<T> hres;
+    int th = 0;
+    double h_ms = 0.0;
+    {
+        int hL = 0, hleaf = b;
+        hodlr_tree(b, h->opts.leaf > 0 ? h->opts.leaf : default_leaf(b), hL, hleaf);
+        if (banded && h->tol > 0 && h->opts.h_levels >= 0 && n > 1 && hL >= 1) {
+            const size_t N = (size_t)n * b;
+            const double* oa = h->op.as<double>() + 3 * N;  // a with a_0 = 0
+            const double* oc = oa + N;                       // c with c_{n-1} = 0
+            // the level-0 diagonals, routed as the solve reads them (even
+            // blocks' A_j, C_j; kept blocks' A_i, C_i), NaN / Inf checked
+            const size_t ne0 = (size_t)(n + 1) / 2, nk0 = (size_t)n / 2;
+            const size_t n4[4] = {ne0 * b, ne0 * b, nk0 * b, nk0 * b};
+            size_t tot = 0;
+            for (int i = 0; i < 4; ++i) { h->hd_off[i] = tot; tot += n4[i]; }
+            CK(h->hdiag.alloc(std::max<size_t>(tot, 1) * sizeof(T), h->stream));
+            DevBuf hbad;
+            CK(hbad.alloc(sizeof(int), s));
+            CK(cudaMemsetAsync(hbad.p, 0, sizeof(int), s));
+            T* hd = h->hdiag.as<T>();
+            CK(stage_diagonals<T>(oa, oc, n, b, hd + h->hd_off[0], hd + h->hd_off[1], hd + h->hd_off[2],
+                                  hd + h->hd_off[3], hbad.as<int>(), dD, s));
+            // contiguous copies of a, c in the factor's precision (row and
+            // column scalings of the level-0 products)
+            DevBuf aTb, cTb;
+            const T* aT = nullptr;
+            const T* cT = nullptr;
+            if constexpr (sizeof(T) == 8) {
+                aT = oa;
+                cT = oc;
+            } else {
+                CK(aTb.alloc(N * sizeof(T), s));
+                CK(cTb.alloc(N * sizeof(T), s));
+                CK(convert_d2f(oa, aTb.as<float>(), (long long)N, s));
+                CK(convert_d2f(oc, cTb.as<float>(), (long long)N, s));
+                aT = aTb.as<T>();
+                cT = cTb.as<T>();
+            }
+            hr.reset(new hred::Red<T>());
+            hr->s = s;
+            hr->b = b;
+            hr->L = hL;
+            hr->leaf = hleaf;
+            // The truncation errors of every level's Schur complements add
+            // up over the reduction: the HODLR arithmetic truncates at tol / 10
+            // (not below a few units of the factor's rounding) to keep the
+            // solve within the 10 tol bound.
+            const double floor_es = sizeof(T) == 8 ? 32 * 2.220446049250313e-16 : 8 * 1.1920929e-7;
+            hr->tol = std::max(h->tol / 10.0, floor_es);
+            hr->kcap = h->opts.max_rank > 0 ? h->opts.max_rank : b;
+            hr->rs.add(dD, (size_t)n * 3 * b * 8);
+            hr->rs.add(aT, N * sizeof(T));
+            hr->rs.add(cT, N * sizeof(T));
+            Events hev;
+            cudaEvent_t he0, he1;
+            CK(hev.make(&he0));
+            CK(hev.make(&he1));
+            CK(cudaEventRecord(he0, s));
+            const long long hl0 = launch_count();
+            const auto hw0 = std::chrono::steady_clock::now();
+            // a level's inverses may miss the identity by at most 1e3 times the
+            // truncation tolerance on random vectors
+            const int hst = hred::reduce<T>(*hr, n, dD, aT, cT, h->opts.h_levels, ACR_HRANK_SWITCH, 1e3 * hr->tol, hres,
+                                            h->band0);
+            h->st.h_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - hw0).count() -
+                              hr->wait_ms;
+            CK(cudaEventRecord(he1, s));
+            const cudaError_t se = cudaStreamSynchronize(s);
+            if (se != cudaSuccess) CK(se);
+            int bad = 0;
+            CK(cudaMemcpy(&bad, hbad.p, sizeof(int), cudaMemcpyDeviceToHost));
+            if (bad) return fail(ACR_ERR_INVALID_ARG, "input holds a NaN or Inf");
+            if (hst) return fail(hr->oom ? ACR_ERR_OOM : ACR_ERR_CUDA, "HODLR arithmetic: %s", hr->err.c_str());
+            if (hres.bad_level >= 0)
+                return fail(ACR_ERR_SINGULAR, "singular eliminated block: level %d, block %d (zero pivot in a HODLR leaf "
+                            "or capacitance matrix)", hres.bad_level, hres.bad_block);
+            th = hres.th;
+            for (size_t q = 0; q < hres.check.size() && q < 32; ++q) h->st.h_check[q] = hres.check[q];
+            float hm = 0.f;
+            cudaEventElapsedTime(&hm, he0, he1);
+            h_ms = hm;
+            h->st.h_levels = th;
+            h->st.h_ms = h_ms;
+            h->st.h_flops = hr->flops;
+            h->st.launches_factor += launch_count() - hl0;
+            if (th > 0) {
+                h->band0 = true;  // level 0 keeps A_i, C_i as diagonals
+            } else {
+                hres = hred::Result<T>();
+                hr.reset();
+                h->hdiag.release();
+            }
+        }
+    }
     const bool b0 = h->band0;
 
     // ---- persistent arena -------------------------------------------------
-    const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev, b0);
+    const size_t arena_bytes = plan_levels(n, b, sizeof(T), h->lev, b0, th);
     CK(h->arena.alloc(arena_bytes, h->stream));
     h->st.factor_bytes = arena_bytes;
     const int T_ = h->levels() - 1;
+    const int t0d = th > 0 ? th : (b0 ? 1 : 0);  // first level reduced with dense products
 
     // ---- temporaries: D_odd, A_even, C_even per level (ping-pong) ---------
     auto temp_blocks = [&](int t) {
         const Level& L = h->lev[t];
-        return (b0 && t == 0) ? (size_t)0 : (size_t)L.nk + 2 * (size_t)L.ne;
+        return (t < th || (b0 && t == 0)) ? (size_t)0 : (size_t)L.nk + 2 * (size_t)L.ne;
     };
     size_t tmax[2] = {0, 0};
     for (int t = 0; t <= T_; ++t) tmax[t & 1] = std::max(tmax[t & 1], temp_blocks(t));
@@ -640,7 +843,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     // ---- problem tables (built on the host, one upload) --------------------
     std::vector<GemmProb<T>> probs;
     std::vector<size_t> g1_off(T_ + 1), g1_cnt(T_ + 1), g2_off(T_ + 1), g2_cnt(T_ + 1);
-    for (int t = (b0 ? 1 : 0); t < T_; ++t) {
+    for (int t = t0d; t < T_; ++t) {
         const Level& L = h->lev[t];
         const Level& Ln = h->lev[t + 1];
         T* dinv = h->P<T>(L.off_dinv);
@@ -699,7 +902,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
                 return (int)(at / mb);
             };
             std::vector<TcProb> tp;
-            for (int t = (b0 ? 1 : 0); t < T_; ++t) {
+            for (int t = t0d; t < T_; ++t) {
                 const Level& L = h->lev[t];
                 const Level& Ln = h->lev[t + 1];
                 const int mDinv = add_map(h->P<T>(L.off_dinv), L.ne, 0), mAev = add_map(t_aev(t), L.ne, 1),
@@ -759,8 +962,34 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     CK(evown.make(&e1));
     CK(cudaEventRecord(e0, s));
 
-    // ---- level 0 staging -----------------------------------------------------
-    {
+    // ---- level 0 staging (or the blocks of level th, from HODLR form) ----------
+    if (th > 0 && th <= T_) {
+        const Level& L = h->lev[th];
+        // even blocks j -> slot j/2 of the eliminated arrays, odd i -> slot i/2
+        // of the kept ones
+        std::vector<int> dev_, dod, aev, cev, ak, ck;
+        for (int j = 0; j < L.m; ++j) {
+            if (j & 1) {
+                dod.push_back(j);
+                ak.push_back(2 * j);
+                ck.push_back(2 * j + 1);
+            } else {
+                dev_.push_back(j);
+                aev.push_back(2 * j);
+                cev.push_back(2 * j + 1);
+            }
+        }
+        hr->rs.add(h->arena.p, arena_bytes);
+        hr->rs.add(tmp[th & 1].p, tmax[th & 1] * blk);
+        int est = hr->expand(*hres.Dn, {{dev_, h->P<T>(L.off_dinv)}, {dod, t_dodd(th)}});
+        if (!est && L.m > 1)
+            est = hr->expand(*hres.ACn, {{aev, t_aev(th)}, {cev, t_cev(th)}, {ak, h->P<T>(L.off_ak)},
+                                         {ck, h->P<T>(L.off_ck)}});
+        if (est) return fail(ACR_ERR_CUDA, "HODLR arithmetic: %s", hr->err.c_str());
+        hres.Dn.reset();
+        hres.ACn.reset();
+        hr->drop_tmp();
+    } else if (th == 0) {
         const Level& L = h->lev[0];
         if (b0) {
             const double* oa = h->op.as<double>() + 3 * (size_t)n * b;  // a with a_0 = 0
@@ -787,7 +1016,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
     };
     const long long l0 = launch_count();
     long long inv_l = 0, gemm_l = 0;
-    for (int t = 0; t <= T_; ++t) {
+    for (int t = th; t <= T_; ++t) {
         const Level& L = h->lev[t];
         long long c0 = launch_count();
         CK(mark(0));
@@ -849,32 +1078,33 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
         cudaEventElapsedTime(&d, evs[i], evs[i + 1]);
         cls_ms[evcls[i]] += d;
     }
-    h->st.factor_ms = ms;
+    h->st.factor_ms = ms + h_ms;
     // structured level 0: O(b^2) per block (tridiagonal inverse: ~3 b^2;
-    // elementwise Schur complement: ~8 b^2 per kept block)
-    const size_t t0 = b0 ? 1 : 0;
+    // elementwise Schur complement: ~8 b^2 per kept block); levels below th:
+    // the HODLR arithmetic's own products (h_flops)
+    const size_t t0 = th > 0 ? (size_t)th : (b0 ? 1 : 0);
     double l0_inv = 0.0, l0_schur = 0.0;
-    if (b0) {
+    if (b0 && th == 0) {
         l0_inv = 3.0 * (double)b * b * h->lev[0].ne;
         l0_schur = 8.0 * (double)b * b * h->lev[0].nk;
     }
     double inv_fl = l0_inv;
     for (size_t t = t0; t < h->lev.size(); ++t) inv_fl += 2.0 * (double)b * b * b * h->lev[t].ne;
-    h->st.factor_flops = factor_flops(h->lev, b, t0) + l0_inv + l0_schur;
+    h->st.factor_flops = factor_flops(h->lev, b, t0) + l0_inv + l0_schur + h->st.h_flops;
     h->st.inv_ms = cls_ms[0];
     h->st.inv_flops = inv_fl;
     h->st.gemm_ms = cls_ms[1];
-    h->st.gemm_flops = h->st.factor_flops - inv_fl - l0_schur;
+    h->st.gemm_flops = h->st.factor_flops - inv_fl - l0_schur - h->st.h_flops;
     h->st.inv_launches = inv_l;
     h->st.gemm_launches = gemm_l;
-    h->st.launches_factor = launch_count() - l0 + 1;  // + the staging kernel
+    h->st.launches_factor += launch_count() - l0 + (th == 0 ? 1 : 0);  // + the staging kernel
     if (h->tol > 0) {
         const long long c0 = launch_count();
         cudaEvent_t ce0, ce1;
         CK(evown.make(&ce0));
         CK(evown.make(&ce1));
         CK(cudaEventRecord(ce0, s));
-        const int st = compress_factor<T>(h);
+        const int st = compress_factor<T>(h, th > 0 ? &hres : nullptr);
         if (st != ACR_OK) return st;
         CK(cudaEventRecord(ce1, s));
         CK(cudaEventSynchronize(ce1));
@@ -1719,6 +1949,7 @@ int acr_factor_ex(int nblk, int blksz, const double* A, const double* D, const d
     if (op.precision < ACR_FP64 || op.precision > ACR_FP32_IR) return fail(ACR_ERR_INVALID_ARG, "unknown precision %d", op.precision);
     if (op.input_kind != ACR_DENSE && op.input_kind != ACR_BANDED) return fail(ACR_ERR_INVALID_ARG, "unknown input_kind %d", op.input_kind);
     if (op.m_stop > 1) return fail(ACR_ERR_INVALID_ARG, "m_stop > 1 is not supported (reduction runs to one block)");
+    if (op.h_levels < -1) return fail(ACR_ERR_INVALID_ARG, "h_levels must be >= -1 (got %d)", op.h_levels);
     if (op.ir_max_iter <= 0) op.ir_max_iter = 20;
     if (!(op.ir_tol > 0)) op.ir_tol = 1e-8;
     {

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace acr {
 
 // Kernel launches issued by this library (all threads); the C ABI reports
@@ -242,4 +244,139 @@ cudaError_t gs_coef(const double* h, double* coef, double* hacc, int n, bool fir
 cudaError_t col_scale(double* v, const double* w, const double* scale, long long N, int nrhs,
                       cudaStream_t s);
 
+}  // namespace acr
+
+// --- HODLR arithmetic of the low reduction levels (k_harith.cu) -------------
+// Batched products of different sizes: C[M x N] = beta * Cin + sum over the
+// problem's terms t0 .. t0 + nt - 1 of alpha * op(A) op(B), op(A) M x K and
+// op(B) K x N; flags bit 0: op(A) = A^T (A stored K x M), bit 1: op(B) = B^T.
+// Cin may be NULL (then beta is ignored) or equal to C.  Column-major
+// operands with the given leading dimensions.
+namespace acr {
+template <class T>
+struct VTerm {
+    const T* A;
+    const T* B;
+    int lda, ldb, K, flags;
+    T alpha;
+};
+template <class T>
+struct VProb {
+    T* C;
+    const T* Cin;
+    int ldc, ldcin, M, N;
+    T beta;
+    int t0, nt;
+};
+// Truncation of one node's low-rank sum U V^T (U, V: s x R, leading
+// dimensions ldu, ldv): Vout (s x wout, ld ldvo) receives the leading right
+// singular vectors of U V^T for the kept rank (sigma_k > tol sigma_1, at most
+// kcap), then zero columns.
+template <class T>
+struct RProb {
+    const T* U;
+    const T* V;
+    T* Vout;
+    int ldu, ldv, ldvo, s, R, wout;
+};
+// dst[r, c] = beta * dst[r, c] + alpha * dv[r] * dc[c] * src[r, c] over
+// rows x cols (dv, dc optional; a NULL src contributes 0).
+template <class T>
+struct CProb {
+    const T* src;
+    T* dst;
+    const T* dv;
+    const T* dc;
+    int lds, ldd, rows, cols;
+    T alpha, beta;
+};
+// One finished node into the solve's pool at dst: U (s x rank), then V^T.
+template <class T>
+struct PProb {
+    const T* U;
+    const T* V;
+    T* dst;
+    int ldu, ldv, s, rank;
+};
+constexpr int HMAXL = 16;
+template <class T>
+struct HBandOut {
+    T* U[HMAXL + 1];
+    T* V[HMAXL + 1];
+};
+// narrow != 0: every problem has N <= 8 (64 x 8 output tiles instead of 64 x 32)
+template <class T>
+cudaError_t vgemm(const VProb<T>* probs, const VTerm<T>* terms, const int2* tiles, long long ntiles, int narrow,
+                  cudaStream_t s);
+// appends the output tiles of problem `prob` (M x N) to `tiles`
+void vgemm_tiles(int prob, int M, int N, bool narrow, std::vector<int2>& tiles);
+template <class T>
+cudaError_t hrecomp(const RProb<T>* probs, int nprob, int smax, int Rmax, int* ranks, double tol, int kcap,
+                    cudaStream_t st);
+size_t hrecomp_smem_bytes(int s, int R, int es);
+// chunks: (problem, chunk) pairs, 2048 elements per chunk (hcopy_chunks)
+template <class T>
+cudaError_t hcopy(const CProb<T>* probs, const int2* chunks, long long nchunks, cudaStream_t s);
+void hcopy_chunks(int prob, long long elems, std::vector<int2>& chunks);
+// FP64 inverses of the leaves of tridiagonal blocks sel[0 .. nsel) of Dband
+// (strictly diagonally dominant rows), written leaf after leaf to out
+template <class T>
+cudaError_t tri_leaf_inverse(const double* Dband, const int* sel, int nsel, int b, int leaf, T* out, cudaStream_t s);
+template <class T>
+cudaError_t hkmat(const T* Tc, double* Kd, int nparent, int K, cudaStream_t s);
+template <class T>
+cudaError_t hband(const double* Dband, int nblk, int b, int L, T* leaves, const HBandOut<T>& o, cudaStream_t s);
+template <class T>
+cudaError_t hpack(const PProb<T>* probs, int nprob, cudaStream_t s);
+}  // namespace acr
+
+// --- template batches of the HODLR arithmetic -------------------------------
+// A batch of problems indexed by (g, i), g < ng (block), i < ni (node or
+// leaf); every operand's address is base + map(g) * gs + f(i) * is with
+// map(g) = gmap ? gmap[g] : g and f(i) = (i >> ishift) ^ ixor.  A negative
+// map value drops the operand: the problem (C) or the term (A, B) is skipped
+// for that block.  The whole batch is one kernel argument: no per-problem
+// descriptors are built or uploaded.
+namespace acr {
+template <class T>
+struct HAddr {
+    const T* base;
+    const int* gmap;
+    long long gs, is;
+    int ishift, ixor, ld, pad;
+};
+constexpr int VT_MAXT = 10;
+template <class T>
+struct VTT {
+    HAddr<T> A, B;
+    int K, flags;  // flags bit 0: op(A) = A^T, bit 1: op(B) = B^T
+    T alpha;
+};
+template <class T>
+struct VPT {
+    HAddr<T> C, Cin;  // Cin.base NULL: no input term
+    int M, N, ni, ng, nt, pad;
+    T beta;
+    VTT<T> t[VT_MAXT];
+};
+// dst = beta dst + alpha * dv[r] * dc[c] * src over rows x cols per problem
+// (src, dv, dc optional: base NULL)
+template <class T>
+struct CPT {
+    HAddr<T> src, dst, dv, dc;
+    int rows, cols, ni, ng;
+    T alpha, beta;
+};
+// truncation of node (g, i): U (s x R, ld), V (s x R), Vout (s x wout)
+template <class T>
+struct RPT {
+    HAddr<T> U, V, Vout;
+    int s, R, wout, ni, ng;
+};
+template <class T>
+cudaError_t vgemm_t(const VPT<T>& P, cudaStream_t s);
+template <class T>
+cudaError_t hcopy_t(const CPT<T>& P, cudaStream_t s);
+template <class T>
+cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, cudaStream_t st);
 }  // namespace acr

@@ -1,0 +1,899 @@
+// k_harith.cu -- batched kernels of the hierarchical (HODLR) arithmetic that
+// reduces the low levels of block cyclic reduction with every block held in
+// compressed form (Section 3: the inverses, products and sums of the
+// reduction are carried out in H-matrix arithmetic, with truncation to the
+// tolerance after each sum).
+//
+// The block format these kernels serve ("stacked" HODLR): a b x b block with
+// L tree levels keeps
+//   - its 2^L diagonal leaves (leaf x leaf, column-major, contiguous);
+//   - per tree level l, two b x K_l column-major panels U_l and V_l (leading
+//     dimension b).  Node i of level l (node size s = b >> l) covers rows
+//     [i s, (i+1) s) and the columns of its sibling i^1; its block is
+//     U_l[rows of i] V_l[rows of i^1]^T.  Columns beyond a node's rank are 0.
+// Restricting a panel to a node's (or a diagonal block's) rows is then a
+// pointer offset, which turns every step of the arithmetic into batches of
+// small dense products over row ranges of these panels.
+//
+// Kernels:
+//   k_vgemm    batched products of different sizes: C = beta Cin + sum_t alpha_t op(A_t) op(B_t)
+//   k_hrecomp  truncation of one low-rank sum U V^T per node: Householder QR of U,
+//              Y = V R_U^T, Householder QR of Y, one-sided Jacobi SVD of R_Y,
+//              V' = Q_Y W (the leading right singular vectors of U V^T, rank by
+//              sigma_k > tol sigma_1); U' = U (V^T V') follows by k_vgemm
+//   k_hcopy    scaled (optionally row-scaled) copies of panels between blocks
+//   k_hkmat    the (2K x 2K) capacitance matrices [[I, T_b], [T_a, I]] of the
+//              Woodbury steps of the inverse, in FP64
+//   k_hband    the level-0 blocks of a 5-point operator in this format
+//   k_hpack    nodes of finished blocks into the solve's pool (U, then V^T)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+// ---------------------------------------------------------------- k_vgemm
+// 64 x 32 output tile per CTA of 256 threads; thread (tx, ty) = (tid & 15,
+// tid >> 4) owns rows tx + 16 i (i < 4) and columns 2 ty + j (j < 2).  Each
+// term's op(A) and op(B) tiles are staged in shared memory 16 k at a time,
+// with the loads ordered along the stored (contiguous) dimension of each
+// operand; alpha is folded into the staged A values.
+constexpr int VG_BM = 64, VG_BN = 32, VG_BK = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_vgemm(const VProb<T>* __restrict__ probs, const VTerm<T>* __restrict__ terms,
+                                               const int2* __restrict__ tiles) {
+    __shared__ T As[VG_BK][VG_BM + 1];
+    __shared__ T Bs[VG_BK][VG_BN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int2 tl = tiles[blockIdx.x];
+    const VProb<T> P = probs[tl.x];
+    const int m0 = (tl.y >> 16) * VG_BM, n0 = (tl.y & 0xffff) * VG_BN;
+    T acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = T(0);
+    for (int t = 0; t < P.nt; ++t) {
+        const VTerm<T> Tm = terms[P.t0 + t];
+        const bool ta = Tm.flags & 1, tb = Tm.flags & 2;
+        for (int k0 = 0; k0 < Tm.K; k0 += VG_BK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                int mm, kk;
+                if (!ta) { mm = e & 63; kk = e >> 6; }
+                else { mm = e >> 4; kk = e & 15; }
+                const int m = m0 + mm, k = k0 + kk;
+                T v = T(0);
+                if (m < P.M && k < Tm.K)
+                    v = ta ? Tm.A[(size_t)k + (size_t)m * Tm.lda] : Tm.A[(size_t)m + (size_t)k * Tm.lda];
+                As[kk][mm] = v * Tm.alpha;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = tid + 256 * q;
+                int nn, kk;
+                if (!tb) { kk = e & 15; nn = e >> 4; }
+                else { nn = e & 31; kk = e >> 5; }
+                const int n = n0 + nn, k = k0 + kk;
+                T v = T(0);
+                if (n < P.N && k < Tm.K)
+                    v = tb ? Tm.B[(size_t)n + (size_t)k * Tm.ldb] : Tm.B[(size_t)k + (size_t)n * Tm.ldb];
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < VG_BK; ++kk) {
+                T a[4], bb[2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+                bb[0] = Bs[kk][2 * ty];
+                bb[1] = Bs[kk][2 * ty + 1];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[i][0] = fma(a[i], bb[0], acc[i][0]);
+                    acc[i][1] = fma(a[i], bb[1], acc[i][1]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int n = n0 + 2 * ty + j;
+        if (n >= P.N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = m0 + tx + 16 * i;
+            if (m >= P.M) continue;
+            T v = acc[i][j];
+            if (P.Cin) v += P.beta * P.Cin[(size_t)m + (size_t)n * P.ldcin];
+            P.C[(size_t)m + (size_t)n * P.ldc] = v;
+        }
+    }
+}
+
+// Narrow outputs (N <= 8, the ranks of most nodes): 64 x 8 tiles, thread
+// (tx, ty) = (tid & 63, tid >> 6) owns row tx and columns 2 ty, 2 ty + 1, so no
+// multiply-add is spent on columns beyond 8.
+constexpr int VN_BN = 8;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_vgemm_n8(const VProb<T>* __restrict__ probs,
+                                                  const VTerm<T>* __restrict__ terms, const int2* __restrict__ tiles) {
+    __shared__ T As[VG_BK][VG_BM + 1];
+    __shared__ T Bs[VG_BK][VN_BN];
+    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+    const int2 tl = tiles[blockIdx.x];
+    const VProb<T> P = probs[tl.x];
+    const int m0 = (tl.y >> 16) * VG_BM, n0 = (tl.y & 0xffff) * VN_BN;
+    T acc0 = T(0), acc1 = T(0);
+    for (int t = 0; t < P.nt; ++t) {
+        const VTerm<T> Tm = terms[P.t0 + t];
+        const bool ta = Tm.flags & 1, tb = Tm.flags & 2;
+        for (int k0 = 0; k0 < Tm.K; k0 += VG_BK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                int mm, kk;
+                if (!ta) { mm = e & 63; kk = e >> 6; }
+                else { mm = e >> 4; kk = e & 15; }
+                const int m = m0 + mm, k = k0 + kk;
+                T v = T(0);
+                if (m < P.M && k < Tm.K)
+                    v = ta ? Tm.A[(size_t)k + (size_t)m * Tm.lda] : Tm.A[(size_t)m + (size_t)k * Tm.lda];
+                As[kk][mm] = v * Tm.alpha;
+            }
+            if (tid < VG_BK * VN_BN) {
+                int nn, kk;
+                if (!tb) { kk = tid & 15; nn = tid >> 4; }
+                else { nn = tid & 7; kk = tid >> 3; }
+                const int n = n0 + nn, k = k0 + kk;
+                T v = T(0);
+                if (n < P.N && k < Tm.K)
+                    v = tb ? Tm.B[(size_t)n + (size_t)k * Tm.ldb] : Tm.B[(size_t)k + (size_t)n * Tm.ldb];
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < VG_BK; ++kk) {
+                const T a = As[kk][tx];
+                acc0 = fma(a, Bs[kk][2 * ty], acc0);
+                acc1 = fma(a, Bs[kk][2 * ty + 1], acc1);
+            }
+            __syncthreads();
+        }
+    }
+    const int m = m0 + tx;
+    if (m >= P.M) return;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int n = n0 + 2 * ty + j;
+        if (n >= P.N) continue;
+        T v = j ? acc1 : acc0;
+        if (P.Cin) v += P.beta * P.Cin[(size_t)m + (size_t)n * P.ldcin];
+        P.C[(size_t)m + (size_t)n * P.ldc] = v;
+    }
+}
+
+template <class T>
+cudaError_t vgemm(const VProb<T>* probs, const VTerm<T>* terms, const int2* tiles, long long ntiles, int narrow,
+                  cudaStream_t s) {
+    long long done = 0;
+    while (done < ntiles) {
+        const int cnt = (int)std::min<long long>(ntiles - done, 1 << 30);
+        if (narrow) k_vgemm_n8<T><<<cnt, 256, 0, s>>>(probs, terms, tiles + done);
+        else k_vgemm<T><<<cnt, 256, 0, s>>>(probs, terms, tiles + done);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+void vgemm_tiles(int prob, int M, int N, bool narrow, std::vector<int2>& tiles) {
+    const int bn = narrow ? VN_BN : VG_BN;
+    const int tm = (M + VG_BM - 1) / VG_BM, tn = (N + bn - 1) / bn;
+    for (int i = 0; i < tm; ++i)
+        for (int j = 0; j < tn; ++j) tiles.push_back(make_int2(prob, (i << 16) | j));
+}
+
+// ---------------------------------------------------------------- k_hrecomp
+template <class T>
+__device__ __forceinline__ T hwarp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Householder QR of the s x c panel P (ld s) in place, LAPACK convention
+// (H_j = I - tau_j v_j v_j^T, v_j[j] = 1 stored over the diagonal): the first
+// min(s, c) reflectors; rdiag receives R's diagonal, the strict upper part of
+// R stays in P.  Called by all 256 threads.
+template <class T>
+__device__ void hh_qr(T* P, int s, int c, T* tau, T* rdiag, T* red, int* flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nr = min(s, c);
+    for (int j = 0; j < nr; ++j) {
+        T* col = P + (size_t)j * s;
+        T part = T(0);
+        for (int r = j + 1 + tid; r < s; r += 256) part += col[r] * col[r];
+        part = hwarp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            T xn2 = T(0);
+            for (int w = 0; w < 8; ++w) xn2 += red[w];
+            const T alpha = col[j];
+            if (xn2 == T(0)) {
+                tau[j] = T(0);
+                rdiag[j] = alpha;
+                red[8] = T(0);
+                *flag = 0;
+            } else {
+                T beta = sqrt(alpha * alpha + xn2);
+                if (alpha > T(0)) beta = -beta;
+                tau[j] = (beta - alpha) / beta;
+                rdiag[j] = beta;
+                red[8] = T(1) / (alpha - beta);
+                *flag = 1;
+            }
+        }
+        __syncthreads();
+        const T scl = red[8];
+        if (*flag)
+            for (int r = j + 1 + tid; r < s; r += 256) col[r] *= scl;
+        __syncthreads();
+        if (tid == 0) col[j] = T(1);
+        __syncthreads();
+        const T tj = tau[j];
+        if (tj != T(0))
+            for (int cc = j + 1 + warp; cc < c; cc += 8) {
+                T* pc = P + (size_t)cc * s;
+                T d = T(0);
+                for (int r = j + lane; r < s; r += 32) d += col[r] * pc[r];
+                d = hwarp_sum(d) * tj;
+                for (int r = j + lane; r < s; r += 32) pc[r] -= d * col[r];
+            }
+        __syncthreads();
+    }
+}
+
+// One CTA per node.  Shared memory: panel s x R | RU r0 x R | RY ke x ke |
+// Z s x HR_KZ | tau, rdiag, sv (ke each) | ord (ke ints); ke = r0 rounded up
+// to even.
+constexpr int HR_KZ = 8;
+
+template <class T>
+size_t hrecomp_smem(int s, int R) {
+    const int r0 = std::min(s, R), ke = r0 + (r0 & 1);
+    return ((size_t)s * R + (size_t)r0 * R + (size_t)ke * ke + (size_t)s * HR_KZ + 3 * (size_t)ke) * sizeof(T) +
+           (size_t)ke * sizeof(int) + 16;
+}
+
+template <class T>
+__device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T tol, int kcap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[9];
+    __shared__ int s_flag;
+    const int s = Pr.s, R = Pr.R, r0 = min(s, R), ke = r0 + (r0 & 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T* Pn = reinterpret_cast<T*>(smem_raw);
+    T* RU = Pn + (size_t)s * R;
+    T* RY = RU + (size_t)r0 * R;
+    T* Z = RY + (size_t)ke * ke;
+    T* tau = Z + (size_t)s * HR_KZ;
+    T* rdg = tau + ke;
+    T* sv = rdg + ke;
+    int* ord = reinterpret_cast<int*>(sv + ke);
+    const int wout = Pr.wout;
+    if (r0 == 0) {
+        for (int e = tid; e < s * wout; e += 256) Pr.Vout[(size_t)(e % s) + (size_t)(e / s) * Pr.ldvo] = T(0);
+        if (tid == 0) *rank_out = 0;
+        return;
+    }
+    // ---- QR of U: keep R_U (r0 x R, upper trapezoidal) -----------------------
+    for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.U[(size_t)(e % s) + (size_t)(e / s) * Pr.ldu];
+    __syncthreads();
+    hh_qr<T>(Pn, s, R, tau, rdg, red, &s_flag);
+    for (int e = tid; e < r0 * R; e += 256) {
+        const int i = e % r0, j = e / r0;
+        RU[e] = (i < j) ? Pn[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
+    }
+    __syncthreads();
+    // ---- Y = V R_U^T in the panel (column c reads V's columns >= c only, so
+    // increasing c may overwrite column c in place; each thread owns its rows)
+    for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
+    __syncthreads();
+    for (int r = tid; r < s; r += 256)
+        for (int c = 0; c < r0; ++c) {
+            T y = T(0);
+            for (int j = c; j < R; ++j) y = fma(Pn[r + (size_t)j * s], RU[c + (size_t)j * r0], y);
+            Pn[r + (size_t)c * s] = y;
+        }
+    __syncthreads();
+    // ---- QR of Y (s x r0): R_Y into RY (ke x ke, zero padded) ----------------
+    hh_qr<T>(Pn, s, r0, tau, rdg, red, &s_flag);
+    for (int e = tid; e < ke * ke; e += 256) {
+        const int i = e % ke, j = e / ke;
+        T v = T(0);
+        if (i < r0 && j < r0) v = (i < j) ? Pn[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
+        RY[e] = v;
+    }
+    __syncthreads();
+    // ---- one-sided Jacobi on the columns of R_Y (round-robin pairs) ----------
+    const T eps = sizeof(T) == 8 ? T(4e-15) : T(4e-7);
+    {
+        T part = T(0);
+        for (int e = tid; e < ke * ke; e += 256) part += RY[e] * RY[e];
+        part = hwarp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            T f = T(0);
+            for (int w = 0; w < 8; ++w) f += red[w];
+            red[8] = f;
+        }
+        __syncthreads();
+    }
+    const T negl = red[8] * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
+    __syncthreads();
+    if (ke >= 2) {
+        for (int sweep = 0; sweep < 16; ++sweep) {
+            if (tid == 0) s_flag = 0;
+            __syncthreads();
+            for (int rnd = 0; rnd < ke - 1; ++rnd) {
+                for (int q = warp; q < ke / 2; q += 8) {
+                    int a, bc;
+                    if (q == 0) { a = ke - 1; bc = rnd; }
+                    else { a = (rnd + q) % (ke - 1); bc = (rnd - q + (ke - 1)) % (ke - 1); }
+                    T* ca = RY + (size_t)a * ke;
+                    T* cb = RY + (size_t)bc * ke;
+                    T al = T(0), be = T(0), ga = T(0);
+                    for (int r = lane; r < ke; r += 32) {
+                        const T x = ca[r], y = cb[r];
+                        al += x * x; be += y * y; ga += x * y;
+                    }
+                    al = hwarp_sum(al); be = hwarp_sum(be); ga = hwarp_sum(ga);
+                    if (al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                        const T zeta = (be - al) / (T(2) * ga);
+                        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+                        for (int r = lane; r < ke; r += 32) {
+                            const T x = ca[r], y = cb[r];
+                            ca[r] = cs * x - sn * y;
+                            cb[r] = sn * x + cs * y;
+                        }
+                        if (lane == 0) s_flag = 1;
+                    }
+                }
+                __syncthreads();
+            }
+            const bool converged = !s_flag;
+            __syncthreads();
+            if (converged) break;
+        }
+    }
+    // ---- singular values, order, rank ------------------------------------------
+    for (int c = warp; c < ke; c += 8) {
+        T n2 = T(0);
+        for (int r = lane; r < ke; r += 32) n2 += RY[r + (size_t)c * ke] * RY[r + (size_t)c * ke];
+        n2 = hwarp_sum(n2);
+        if (lane == 0) sv[c] = sqrt(n2);
+    }
+    __syncthreads();
+    for (int c = tid; c < ke; c += 256) {  // decreasing, ties by index, NaN last
+        const T vc = isnan(sv[c]) ? T(-1) : sv[c];
+        int pos = 0;
+        for (int j = 0; j < ke; ++j) {
+            const T vj = isnan(sv[j]) ? T(-1) : sv[j];
+            pos += (vj > vc) || (vj == vc && j < c);
+        }
+        ord[pos] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const T s1 = sv[ord[0]];
+        int r = 0;
+        if (s1 > T(0) && !isnan(s1))
+            while (r < ke && r < wout && r < kcap && sv[ord[r]] > tol * s1) ++r;
+        s_flag = r;
+        *rank_out = r;
+    }
+    __syncthreads();
+    const int rk = s_flag;
+    // ---- V' = Q_Y [W; 0] for the kept columns, HR_KZ at a time -----------------
+    for (int c0 = 0; c0 < wout; c0 += HR_KZ) {
+        const int nc = min(HR_KZ, wout - c0);
+        for (int e = tid; e < s * nc; e += 256) {
+            const int r = e % s, c = e / s, cg = c0 + c;
+            T v = T(0);
+            if (cg < rk && r < r0) {
+                const int src = ord[cg];
+                const T nv = sv[src];
+                v = nv > T(0) ? RY[r + (size_t)src * ke] / nv : T(0);
+            }
+            Z[r + (size_t)c * s] = v;
+        }
+        __syncthreads();
+        if (c0 < rk)
+            for (int j = r0 - 1; j >= 0; --j) {
+                const T tj = tau[j];
+                if (tj == T(0)) continue;
+                const T* v = Pn + (size_t)j * s;
+                for (int c = warp; c < nc; c += 8) {
+                    T* zc = Z + (size_t)c * s;
+                    T d = T(0);
+                    for (int r = j + lane; r < s; r += 32) d += v[r] * zc[r];
+                    d = hwarp_sum(d) * tj;
+                    for (int r = j + lane; r < s; r += 32) zc[r] -= d * v[r];
+                }
+                __syncthreads();
+            }
+        for (int e = tid; e < s * nc; e += 256) {
+            const int r = e % s, c = e / s;
+            Pr.Vout[(size_t)r + (size_t)(c0 + c) * Pr.ldvo] = (c0 + c < rk) ? Z[r + (size_t)c * s] : T(0);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_hrecomp(const RProb<T>* __restrict__ probs, int* __restrict__ ranks, T tol,
+                                                 int kcap) {
+    hrecomp_body<T>(probs[blockIdx.x], ranks + blockIdx.x, tol, kcap);
+}
+
+template <class T>
+cudaError_t hrecomp(const RProb<T>* probs, int nprob, int smax, int Rmax, int* ranks, double tol, int kcap,
+                    cudaStream_t st) {
+    if (nprob <= 0) return cudaSuccess;
+    const size_t sm = hrecomp_smem<T>(smax, Rmax);
+    if (sm > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem((const void*)k_hrecomp<T>, sm);
+    if (e != cudaSuccess) return e;
+    int done = 0;
+    while (done < nprob) {
+        const int cnt = std::min(nprob - done, 1 << 30);
+        k_hrecomp<T><<<cnt, 256, sm, st>>>(probs + done, ranks + done, (T)tol, kcap);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+size_t hrecomp_smem_bytes(int s, int R, int es) {
+    return es == 8 ? hrecomp_smem<double>(s, R) : hrecomp_smem<float>(s, R);
+}
+
+// ---------------------------------------------------------------- k_hcopy
+// dst[r, c] = beta * dst[r, c] + alpha * dv[r] * dc[c] * src[r, c] (dv, dc
+// optional; a NULL src contributes 0; beta == 0 does not read dst), rows x
+// cols per problem.  One CTA per chunk of 2048 consecutive elements (column
+// after column) of one problem: chunks[i] = (problem, first element / 2048).
+template <class T>
+__global__ void __launch_bounds__(256) k_hcopy(const CProb<T>* __restrict__ probs, const int2* __restrict__ chunks) {
+    const int2 ch = chunks[blockIdx.x];
+    const CProb<T> P = probs[ch.x];
+    const int n = P.rows * P.cols;
+    const int e0 = ch.y * 2048;
+    const int e1 = min(n, e0 + 2048);
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += 256) {
+        const int c = e / P.rows, r = e - c * P.rows;
+        T v = T(0);
+        if (P.src) {
+            v = P.alpha * P.src[(size_t)r + (size_t)c * P.lds];
+            if (P.dv) v *= P.dv[r];
+            if (P.dc) v *= P.dc[c];
+        }
+        T* d = P.dst + (size_t)r + (size_t)c * P.ldd;
+        if (P.beta != T(0)) v += P.beta * *d;
+        *d = v;
+    }
+}
+
+template <class T>
+cudaError_t hcopy(const CProb<T>* probs, const int2* chunks, long long nchunks, cudaStream_t s) {
+    long long done = 0;
+    while (done < nchunks) {
+        const int cnt = (int)std::min<long long>(nchunks - done, 1 << 30);
+        k_hcopy<T><<<cnt, 256, 0, s>>>(probs, chunks + done);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+void hcopy_chunks(int prob, long long elems, std::vector<int2>& chunks) {
+    for (long long e = 0; e < elems; e += 2048) chunks.push_back(make_int2(prob, (int)(e / 2048)));
+}
+
+// ---------------------------------------------------------------- leaf inverses
+// FP64 inverse of every leaf of a tridiagonal block (level 0 of a 5-point
+// operator): leaf (g, lam) covers rows [lam leaf, (lam+1) leaf) of D_{sel[g]}
+// (Dband: [sub, diag, super] per block).  The leaf's LU factors (no pivoting:
+// used only for strictly diagonally dominant rows, where they are stable) are
+// formed once; thread c solves L y = e_c forward (y kept in shared memory,
+// ld leaf + 1) and U x = y backward, writing x over y; the leaf's inverse is
+// then stored column after column with coalesced writes.  O(leaf^2) per leaf.
+template <class T>
+__global__ void __launch_bounds__(128) k_tri_leaf_inv(const double* __restrict__ Dband, const int* __restrict__ sel,
+                                                      int b, int leaf, T* __restrict__ out) {
+    extern __shared__ double tl_sm[];
+    double* lo = tl_sm;        // multipliers l_r (r >= 1)
+    double* dg = lo + leaf;    // pivots u_r
+    double* up = dg + leaf;    // super-diagonal
+    double* Y = up + leaf;     // leaf x leaf, ld leaf + 1
+    const int ld = leaf + 1;
+    const int nl = b / leaf;
+    const int g = blockIdx.x / nl, lam = blockIdx.x % nl;
+    const double* sub = Dband + (size_t)sel[g] * 3 * b + (size_t)lam * leaf;
+    const double* dia = sub + b;
+    const double* sup = dia + b;
+    for (int r = threadIdx.x; r < leaf; r += blockDim.x) up[r] = sup[r];
+    if (threadIdx.x == 0) {
+        double u = dia[0];
+        dg[0] = u;
+        lo[0] = 0.0;
+        for (int r = 1; r < leaf; ++r) {
+            const double l = sub[r] / u;
+            lo[r] = l;
+            u = dia[r] - l * sup[r - 1];
+            dg[r] = u;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < leaf; c += blockDim.x) {
+        double* y = Y + (size_t)c * ld;
+        double v = 1.0;
+        y[c] = 1.0;
+        for (int r = c + 1; r < leaf; ++r) {
+            v = -lo[r] * v;
+            y[r] = v;
+        }
+        double xn = 0.0;
+        for (int r = leaf - 1; r >= 0; --r) {
+            const double yr = r >= c ? y[r] : 0.0;
+            const double xr = (yr - (r + 1 < leaf ? up[r] * xn : 0.0)) / dg[r];
+            y[r] = xr;
+            xn = xr;
+        }
+    }
+    __syncthreads();
+    T* o = out + (size_t)blockIdx.x * leaf * leaf;
+    for (int e = threadIdx.x; e < leaf * leaf; e += blockDim.x) {
+        const int c = e / leaf, r = e - c * leaf;
+        o[e] = (T)Y[(size_t)c * ld + r];
+    }
+}
+
+template <class T>
+cudaError_t tri_leaf_inverse(const double* Dband, const int* sel, int nsel, int b, int leaf, T* out, cudaStream_t s) {
+    if (nsel <= 0) return cudaSuccess;
+    const long long nb = (long long)nsel * (b / leaf);
+    if (nb > (1LL << 30)) return cudaErrorInvalidValue;
+    long long done = 0;
+    while (done < nb) {
+        const int cnt = (int)std::min<long long>(nb - done, 1 << 30);
+        const size_t sm = (3 * (size_t)leaf + (size_t)leaf * (leaf + 1)) * sizeof(double);
+        ensure_smem((const void*)k_tri_leaf_inv<T>, sm);
+        k_tri_leaf_inv<T><<<cnt, 128, sm, s>>>(Dband, sel, b, leaf, out + (size_t)done * leaf * leaf);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- k_hkmat
+// Kd[p] (2K x 2K, FP64, column-major) = [[I, T_{2p+1}], [T_{2p}, I]] from the
+// K x K cores Tc (column-major, node after node); one CTA per parent.
+template <class T>
+__global__ void k_hkmat(const T* __restrict__ Tc, double* __restrict__ Kd, int K) {
+    const size_t p = blockIdx.x;
+    const T* Ta = Tc + (2 * p) * (size_t)K * K;
+    const T* Tb = Ta + (size_t)K * K;
+    double* out = Kd + p * (size_t)4 * K * K;
+    const int K2 = 2 * K;
+    for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) {
+        const int r = e % K2, c = e / K2;
+        double v;
+        if (r < K && c >= K) v = (double)Tb[r + (size_t)(c - K) * K];
+        else if (r >= K && c < K) v = (double)Ta[(r - K) + (size_t)c * K];
+        else v = (r == c) ? 1.0 : 0.0;
+        out[e] = v;
+    }
+}
+
+template <class T>
+cudaError_t hkmat(const T* Tc, double* Kd, int nparent, int K, cudaStream_t s) {
+    if (nparent <= 0 || K <= 0) return cudaSuccess;
+    int done = 0;
+    while (done < nparent) {
+        const int cnt = std::min(nparent - done, 1 << 30);
+        k_hkmat<T><<<cnt, 256, 0, s>>>(Tc + (size_t)done * 2 * K * K, Kd + (size_t)done * 4 * K * K, K);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- k_hband
+// Level-0 block D_g of a 5-point operator (tridiagonal: Dband = [sub, diag,
+// super] per block) in the stacked format with one column per tree level:
+// leaves hold the tridiagonal's diagonal blocks, the upper node 2p of level
+// l is the single entry super[(2p+1)s - 1] at (last row of 2p, first column of
+// 2p+1), the lower node 2p+1 the entry sub[(2p+1)s] at (first row of 2p+1,
+// last column of 2p).  U_l, V_l of block g at Ul[l-1] + g*b, Vl[l-1] + g*b.
+template <class T>
+__global__ void k_hband(const double* __restrict__ Dband, int b, int L, T* __restrict__ leaves, HBandOut<T> o) {
+    const int g = blockIdx.x;
+    const int leaf = b >> L;
+    const double* sub = Dband + (size_t)g * 3 * b;
+    const double* dg = sub + b;
+    const double* sup = dg + b;
+    T* lv = leaves + (size_t)g * b * leaf;
+    for (int e = threadIdx.x; e < b * leaf; e += blockDim.x) {
+        const int lam = e / (leaf * leaf), w = e % (leaf * leaf);
+        const int r = w % leaf, c = w / leaf, gr = lam * leaf + r, gc = lam * leaf + c;
+        double v = 0.0;
+        if (r == c) v = dg[gr];
+        else if (c == r + 1) v = sup[gr];
+        else if (r == c + 1) v = sub[gr];
+        (void)gc;
+        lv[e] = (T)v;
+    }
+    for (int l = 1; l <= L; ++l) {
+        const int s = b >> l;
+        T* U = o.U[l] + (size_t)g * b;
+        T* V = o.V[l] + (size_t)g * b;
+        for (int r = threadIdx.x; r < b; r += blockDim.x) {
+            const int i = r / s, w = r % s;
+            T u = T(0), v = T(0);
+            if ((i & 1) == 0) {       // upper node i: its U row (last of i), and node i+1's V row (last of i)
+                if (w == s - 1) { u = (T)sup[r]; v = T(1); }
+            } else {                  // lower node i: its U row (first of i), and node i-1's V row (first of i)
+                if (w == 0) { u = (T)sub[r]; v = T(1); }
+            }
+            U[r] = u;
+            V[r] = v;
+        }
+    }
+}
+
+template <class T>
+cudaError_t hband(const double* Dband, int nblk, int b, int L, T* leaves, const HBandOut<T>& o, cudaStream_t s) {
+    if (nblk <= 0) return cudaSuccess;
+    k_hband<T><<<nblk, 256, 0, s>>>(Dband, b, L, leaves, o);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- k_hpack
+// One node into the solve's pool: U (s x rank, column-major), then V stored
+// transposed (rank x s), the layout the compressed sweeps read.
+template <class T>
+__global__ void __launch_bounds__(256) k_hpack(const PProb<T>* __restrict__ probs) {
+    const PProb<T> P = probs[blockIdx.x];
+    const int n = P.s * P.rank;
+    for (int e = threadIdx.x; e < n; e += 256) {
+        P.dst[e] = P.U[(size_t)(e % P.s) + (size_t)(e / P.s) * P.ldu];
+        const int ii = e % P.rank, j = e / P.rank;
+        P.dst[n + e] = P.V[(size_t)j + (size_t)ii * P.ldv];
+    }
+}
+
+template <class T>
+cudaError_t hpack(const PProb<T>* probs, int nprob, cudaStream_t s) {
+    int done = 0;
+    while (done < nprob) {
+        const int cnt = std::min(nprob - done, 1 << 30);
+        k_hpack<T><<<cnt, 256, 0, s>>>(probs + done);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t vgemm<float>(const VProb<float>*, const VTerm<float>*, const int2*, long long, int, cudaStream_t);
+template cudaError_t vgemm<double>(const VProb<double>*, const VTerm<double>*, const int2*, long long, int,
+                                   cudaStream_t);
+template cudaError_t hrecomp<float>(const RProb<float>*, int, int, int, int*, double, int, cudaStream_t);
+template cudaError_t hrecomp<double>(const RProb<double>*, int, int, int, int*, double, int, cudaStream_t);
+template cudaError_t hcopy<float>(const CProb<float>*, const int2*, long long, cudaStream_t);
+template cudaError_t hcopy<double>(const CProb<double>*, const int2*, long long, cudaStream_t);
+template cudaError_t tri_leaf_inverse<float>(const double*, const int*, int, int, int, float*, cudaStream_t);
+template cudaError_t tri_leaf_inverse<double>(const double*, const int*, int, int, int, double*, cudaStream_t);
+template cudaError_t hkmat<float>(const float*, double*, int, int, cudaStream_t);
+template cudaError_t hkmat<double>(const double*, double*, int, int, cudaStream_t);
+template cudaError_t hband<float>(const double*, int, int, int, float*, const HBandOut<float>&, cudaStream_t);
+template cudaError_t hband<double>(const double*, int, int, int, double*, const HBandOut<double>&, cudaStream_t);
+template cudaError_t hpack<float>(const PProb<float>*, int, cudaStream_t);
+template cudaError_t hpack<double>(const PProb<double>*, int, cudaStream_t);
+
+}  // namespace acr
+
+// =============================================================================
+// Template batches: the problem (g, i) of a batch is derived from blockIdx and
+// its operands' addresses from the batch's strides (see HAddr).
+// =============================================================================
+namespace acr {
+
+template <class T>
+__device__ __forceinline__ const T* haddr(const HAddr<T>& a, int g, int i) {
+    if (!a.base) return nullptr;
+    const long long gg = a.gmap ? (long long)a.gmap[g] : (long long)g;
+    if (gg < 0) return nullptr;
+    return a.base + gg * a.gs + (long long)((i >> a.ishift) ^ a.ixor) * a.is;
+}
+
+template <class T, bool NARROW>
+__global__ void __launch_bounds__(256) k_vgemm_t(const __grid_constant__ VPT<T> P, int tpm, int tpn) {
+    constexpr int BN = NARROW ? VN_BN : VG_BN;
+    __shared__ T As[VG_BK][VG_BM + 1];
+    __shared__ T Bs[VG_BK][BN + (NARROW ? 0 : 1)];
+    const int tid = threadIdx.x;
+    const long long tpp = (long long)tpm * tpn;
+    const long long p = blockIdx.x / tpp;
+    const int tt = (int)(blockIdx.x - p * tpp);
+    const int g = (int)(p / P.ni), i = (int)(p - (long long)g * P.ni);
+    T* C = const_cast<T*>(haddr(P.C, g, i));
+    if (!C) return;
+    const T* Cin = haddr(P.Cin, g, i);
+    const int m0 = (tt / tpn) * VG_BM, n0 = (tt % tpn) * BN;
+    // thread layout: wide tiles as k_vgemm (4 rows x 2 columns), narrow tiles
+    // as k_vgemm_n8 (1 row x 2 columns)
+    const int tx = NARROW ? (tid & 63) : (tid & 15), ty = NARROW ? (tid >> 6) : (tid >> 4);
+    constexpr int RI = NARROW ? 1 : 4;
+    T acc[RI][2];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) acc[r][0] = acc[r][1] = T(0);
+    for (int t = 0; t < P.nt; ++t) {
+        const VTT<T>& Tm = P.t[t];
+        const T* A = haddr(Tm.A, g, i);
+        const T* B = haddr(Tm.B, g, i);
+        if (!A || !B) continue;  // uniform over the CTA
+        const bool ta = Tm.flags & 1, tb = Tm.flags & 2;
+        const int lda = Tm.A.ld, ldb = Tm.B.ld;
+        for (int k0 = 0; k0 < Tm.K; k0 += VG_BK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                int mm, kk;
+                if (!ta) { mm = e & 63; kk = e >> 6; }
+                else { mm = e >> 4; kk = e & 15; }
+                const int m = m0 + mm, k = k0 + kk;
+                T v = T(0);
+                if (m < P.M && k < Tm.K) v = ta ? A[(size_t)k + (size_t)m * lda] : A[(size_t)m + (size_t)k * lda];
+                As[kk][mm] = v * Tm.alpha;
+            }
+            for (int e = tid; e < VG_BK * BN; e += 256) {
+                int nn, kk;
+                if (!tb) { kk = e & 15; nn = e >> 4; }
+                else { nn = e % BN; kk = e / BN; }
+                const int n = n0 + nn, k = k0 + kk;
+                T v = T(0);
+                if (n < P.N && k < Tm.K) v = tb ? B[(size_t)n + (size_t)k * ldb] : B[(size_t)k + (size_t)n * ldb];
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < VG_BK; ++kk) {
+                const T b0 = Bs[kk][2 * ty], b1 = Bs[kk][2 * ty + 1];
+#pragma unroll
+                for (int r = 0; r < RI; ++r) {
+                    const T a = As[kk][tx + (NARROW ? 0 : 16 * r)];
+                    acc[r][0] = fma(a, b0, acc[r][0]);
+                    acc[r][1] = fma(a, b1, acc[r][1]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int n = n0 + 2 * ty + j;
+        if (n >= P.N) continue;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int m = m0 + tx + (NARROW ? 0 : 16 * r);
+            if (m >= P.M) continue;
+            T v = acc[r][j];
+            if (Cin) v += P.beta * Cin[(size_t)m + (size_t)n * P.Cin.ld];
+            C[(size_t)m + (size_t)n * P.C.ld] = v;
+        }
+    }
+}
+
+template <class T>
+cudaError_t vgemm_t(const VPT<T>& P, cudaStream_t s) {
+    if (P.M <= 0 || P.N <= 0 || P.ni <= 0 || P.ng <= 0) return cudaSuccess;
+    const bool narrow = P.N <= VN_BN;
+    const int tpm = (P.M + VG_BM - 1) / VG_BM, tpn = (P.N + (narrow ? VN_BN : VG_BN) - 1) / (narrow ? VN_BN : VG_BN);
+    const long long n = (long long)P.ng * P.ni * tpm * tpn;
+    if (n >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (narrow) k_vgemm_t<T, true><<<(unsigned)n, 256, 0, s>>>(P, tpm, tpn);
+    else k_vgemm_t<T, false><<<(unsigned)n, 256, 0, s>>>(P, tpm, tpn);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_hcopy_t(const __grid_constant__ CPT<T> P, int cpp) {
+    const long long p = blockIdx.x / cpp;
+    const int ch = (int)(blockIdx.x - p * cpp);
+    const int g = (int)(p / P.ni), i = (int)(p - (long long)g * P.ni);
+    T* dst = const_cast<T*>(haddr(P.dst, g, i));
+    if (!dst) return;
+    const T* src = haddr(P.src, g, i);
+    const T* dv = haddr(P.dv, g, i);
+    const T* dc = haddr(P.dc, g, i);
+    const int n = P.rows * P.cols;
+    const int e1 = min(n, (ch + 1) * 2048);
+    for (int e = ch * 2048 + (int)threadIdx.x; e < e1; e += 256) {
+        const int c = e / P.rows, r = e - c * P.rows;
+        T v = T(0);
+        if (src) {
+            v = P.alpha * src[(size_t)r + (size_t)c * P.src.ld];
+            if (dv) v *= dv[r];
+            if (dc) v *= dc[c];
+        }
+        T* d = dst + (size_t)r + (size_t)c * P.dst.ld;
+        if (P.beta != T(0)) v += P.beta * *d;
+        *d = v;
+    }
+}
+
+template <class T>
+cudaError_t hcopy_t(const CPT<T>& P, cudaStream_t s) {
+    const long long el = (long long)P.rows * P.cols;
+    if (el <= 0 || P.ni <= 0 || P.ng <= 0) return cudaSuccess;
+    if (el >= (1LL << 31)) return cudaErrorInvalidValue;
+    const int cpp = (int)((el + 2047) / 2048);
+    const long long n = (long long)P.ng * P.ni * cpp;
+    if (n >= (1LL << 31)) return cudaErrorInvalidValue;
+    k_hcopy_t<T><<<(unsigned)n, 256, 0, s>>>(P, cpp);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// one node per CTA; the body is k_hrecomp's
+template <class T>
+__global__ void __launch_bounds__(256) k_hrecomp_t(const __grid_constant__ RPT<T> P, int* __restrict__ ranks, T tol,
+                                                   int kcap) {
+    const int node = blockIdx.x;
+    const int g = node / P.ni, i = node - g * P.ni;
+    RProb<T> q;
+    q.U = haddr(P.U, g, i);
+    q.V = haddr(P.V, g, i);
+    q.Vout = const_cast<T*>(haddr(P.Vout, g, i));
+    q.ldu = P.U.ld;
+    q.ldv = P.V.ld;
+    q.ldvo = P.Vout.ld;
+    q.s = P.s;
+    q.R = P.R;
+    q.wout = P.wout;
+    hrecomp_body<T>(q, ranks + node, tol, kcap);
+}
+
+template <class T>
+cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, cudaStream_t st) {
+    const long long n = (long long)P.ng * P.ni;
+    if (n <= 0) return cudaSuccess;
+    if (n >= (1LL << 31)) return cudaErrorInvalidValue;
+    const size_t sm = hrecomp_smem<T>(P.s, P.R);
+    if (sm > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem((const void*)k_hrecomp_t<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_hrecomp_t<T><<<(unsigned)n, 256, sm, st>>>(P, ranks, (T)tol, kcap);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t vgemm_t<float>(const VPT<float>&, cudaStream_t);
+template cudaError_t vgemm_t<double>(const VPT<double>&, cudaStream_t);
+template cudaError_t hcopy_t<float>(const CPT<float>&, cudaStream_t);
+template cudaError_t hcopy_t<double>(const CPT<double>&, cudaStream_t);
+template cudaError_t hrecomp_t<float>(const RPT<float>&, int*, double, int, cudaStream_t);
+template cudaError_t hrecomp_t<double>(const RPT<double>&, int*, double, int, cudaStream_t);
+
+}  // namespace acr

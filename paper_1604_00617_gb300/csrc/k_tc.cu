@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include <atomic>
 #include <mutex>
 #include <cstdint>
@@ -61,9 +63,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Bounded wait for the phase with parity `ph`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph, long long limit) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -135,7 +137,8 @@ using namespace tc;
 // so a launch can leave out a band of column tiles (nskip = INT_MAX: no band).
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps, int b, int tiles_m,
-          int* __restrict__ err, int kdim, int ka0, int nskip, int nshift, int lolo) {
+          int* __restrict__ err, int kdim, int ka0, int nskip, int nshift, int lolo, long long wlimit,
+          int withhold) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* raw = base;                           // [RAW][A_raw | B_raw]
@@ -182,10 +185,12 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
     const uint32_t tmem_d = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
+        // withhold != 0 (failure-path tests only): no copies are issued, so
+        // every consumer wait runs out and the CTA takes its timeout path
+        if (lane == 0 && !withhold) {
             for (int it = 0; it < niter; ++it) {
                 const int r = it % RAW;
-                if (it >= RAW && !mbar_wait(&raw_free[r], (uint32_t)(((it / RAW) & 1) ^ 1))) { s_fail = 1; break; }
+                if (it >= RAW && !mbar_wait(&raw_free[r], (uint32_t)(((it / RAW) & 1) ^ 1), wlimit)) { s_fail = 1; break; }
                 unsigned char* st = raw + r * RAW_BYTES;
                 const int term = it / kt, kq = (it % kt) * BK;
                 mbar_expect_tx(&full[r], 2 * TILE_BYTES);
@@ -197,7 +202,7 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
         if (lane == 0) {
             for (int it = 0; it < niter; ++it) {
                 const int c = it % CONV;
-                if (!mbar_wait(&conv_full[c], (uint32_t)((it / CONV) & 1))) { s_fail = 1; break; }
+                if (!mbar_wait(&conv_full[c], (uint32_t)((it / CONV) & 1), wlimit)) { s_fail = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 unsigned char* cv = cvt + c * CONV_BYTES;
                 const uint32_t a_hi = smem_u32(cv);
@@ -223,8 +228,8 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
         const int am = t & (BM - 1), ah = t >> 7;  // A: row am, k chunks [4 ah, 4 ah + 4)
         for (int it = 0; it < niter; ++it) {
             const int r = it % RAW, c = it % CONV;
-            if (!mbar_wait(&full[r], (uint32_t)((it / RAW) & 1))) { s_fail = 1; break; }
-            if (it >= CONV && !mbar_wait(&conv_free[c], (uint32_t)(((it / CONV) & 1) ^ 1))) { s_fail = 1; break; }
+            if (!mbar_wait(&full[r], (uint32_t)((it / RAW) & 1), wlimit)) { s_fail = 1; break; }
+            if (it >= CONV && !mbar_wait(&conv_free[c], (uint32_t)(((it / CONV) & 1) ^ 1), wlimit)) { s_fail = 1; break; }
             const unsigned char* st = raw + r * RAW_BYTES;
             unsigned char* cv = cvt + c * CONV_BYTES;
             const float* araw = reinterpret_cast<const float*>(st);   // [k][m], 32 x 128
@@ -268,7 +273,7 @@ k_gemm_tc(const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps
             }
         }
         // ---- epilogue ---------------------------------------------------------
-        const bool ok = mbar_wait(accb, 0);
+        const bool ok = mbar_wait(accb, 0, wlimit);
         if (!ok) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q = warp & 3;  // TMEM lane quarter this warp may read
@@ -371,8 +376,14 @@ cudaError_t gemm_tc_ex(const TcProb* d_probs, int nprob, const void* d_maps, int
     ensure_smem((const void*)k_gemm_tc, SMEM_BYTES);
     const int tiles_m = b / BM;
     dim3 g(tiles_m * tiles_n, nprob);
+    // ACR_TEST_TC_WITHHOLD=1 (failure-path tests): the producer issues no
+    // copies and every wait gives up after a short limit, exercising the
+    // bounded-wait path that ends in ACR_ERR_TIMEOUT with the context usable
+    const char* wh = getenv("ACR_TEST_TC_WITHHOLD");
+    const int withhold = (wh && wh[0] == '1') ? 1 : 0;
+    const long long wlimit = withhold ? (1LL << 12) : WAIT_LIMIT;
     k_gemm_tc<<<g, NTHREADS, SMEM_BYTES, s>>>(d_probs, static_cast<const CUtensorMap*>(d_maps), b, tiles_m, d_err,
-                                              kdim, ka0, nskip, nshift, lolo);
+                                              kdim, ka0, nskip, nshift, lolo, wlimit, withhold);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -120,7 +120,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, slots: int = 4, precision: int = acr.ACR_FP32TC_IR,
                  ir_tol: float = 1e-8, ir_max_iter: int = 60, max_batch: int = 64,
-                 keep_results: bool = False, lib=None, new_stream=None):
+                 keep_results: bool = False, lib=None, new_stream=None, solve_slots: int = 1):
         # `lib` and `new_stream` replace the CUDA library and torch's stream
         # constructor (host-side tests of the scheduling)
         self.lib = lib if lib is not None else acr
@@ -133,6 +133,10 @@ class Server:
         self.new_stream = new_stream
         self.budget = int(budget_bytes)
         self.slots = slots
+        # slots factorizations may not take: solves on resident systems never
+        # wait behind a full set of factorizations (with one slot, none is kept)
+        self.solve_slots = min(max(0, solve_slots), max(0, slots - 1))
+        self.factoring = 0
         self.precision = precision
         self.ir_tol = ir_tol
         self.ir_max_iter = ir_max_iter
@@ -196,6 +200,7 @@ class Server:
             self.errors.append((req.rid, str(e)))
         rec.done = time.perf_counter()
         with self.cv:
+            self.factoring -= 1
             self.reserved -= est
             if h is not None:
                 self.reserved += held
@@ -272,7 +277,7 @@ class Server:
                 self.peak_reserved = max(self.peak_reserved, self.reserved)
                 self.peak_active = max(self.peak_active, self.active)
                 started.append(threading.Thread(target=self._run_solves, args=(sys_rid, batch, ws)))
-        while self.sys_queue and self.active < self.slots:
+        while self.sys_queue and self.active < self.slots and self.factoring < self.slots - self.solve_slots:
             req = self.sys_queue[0]
             est = peak_bytes(req, self.precision)
             if self.reserved + est > self.budget and self.reserved > 0:
@@ -282,6 +287,7 @@ class Server:
             self.reserved += est
             self.peak_reserved = max(self.peak_reserved, self.reserved)
             self.active += 1
+            self.factoring += 1
             self.peak_active = max(self.peak_active, self.active)
             started.append(threading.Thread(target=self._run_factor, args=(req, est, self._stream())))
         for t in started:

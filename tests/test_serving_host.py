@@ -101,10 +101,25 @@ def test_continuous_admission_overlaps():
     # system 1 arrives while system 0 factors: it starts before 0 finishes
     lib = FakeLib(tf=0.3)
     ev = _stream([(0.0, 8, [0.35]), (0.02, 8, [0.36])])
-    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream, solve_slots=0)
     recs, _ = srv.run(ev)
     assert recs[2].start < recs[0].done
     assert lib.max_live == 2 and srv.peak_active == 2
+
+
+def test_solve_slot_kept_free_of_factorizations():
+    # system 0 is resident at 0.3; systems 1 and 2 queue at 0.31 / 0.32 and
+    # its solve arrives at 0.35.  With one of two slots kept for solves, system
+    # 1 factors alone, system 2 waits, and the solve starts at once instead of
+    # waiting for a factorization to end.
+    lib = FakeLib(tf=0.3, ts=0.01)
+    ev = _stream([(0.0, 8, [0.35]), (0.31, 8, [0.9]), (0.32, 8, [0.95])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    recs, _ = srv.run(ev)
+    solve0, fac1, fac2 = recs[1], recs[2], recs[4]
+    assert solve0.start < fac1.done and solve0.start - solve0.arrival < 0.1
+    assert fac2.start >= fac1.done  # never two factorizations at once
+    assert all(r.ok for r in recs.values())
 
 
 def test_solves_coalesced_while_factoring():
