@@ -105,7 +105,7 @@ typedef struct {
 /* Largest off-diagonal rank of a level's blocks for which the automatic
  * choice (h_levels = 0) continues in HODLR arithmetic.  A level also goes
  * dense when its HODLR inverses miss the identity on random vectors by more
- * than 1e3 times the truncation tolerance (see h_check in acr_stats_t).  The
+ * than 1e4 times the truncation tolerance (see h_check in acr_stats_t).  The
  * HODLR arithmetic truncates at max(tol / 10, a few units of the factor's
  * rounding), so that the truncations accumulated over the levels keep the
  * solve near tol. */

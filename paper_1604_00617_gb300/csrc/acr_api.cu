@@ -773,9 +773,9 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
             CK(cudaEventRecord(he0, s));
             const long long hl0 = launch_count();
             const auto hw0 = std::chrono::steady_clock::now();
-            // a level's inverses may miss the identity by at most 1e3 times the
+            // a level's inverses may miss the identity by at most 1e4 times the
             // truncation tolerance on random vectors
-            const int hst = hred::reduce<T>(*hr, n, dD, aT, cT, h->opts.h_levels, ACR_HRANK_SWITCH, 1e3 * hr->tol, hres,
+            const int hst = hred::reduce<T>(*hr, n, dD, aT, cT, h->opts.h_levels, ACR_HRANK_SWITCH, 1e4 * hr->tol, hres,
                                             h->band0);
             h->st.h_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - hw0).count() -
                               hr->wait_ms;

@@ -40,6 +40,7 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -262,6 +263,7 @@ struct Red {
     }
     // Host check that every (g, i) address of an operand, with its rows x cols
     // extent, lies in one registered device buffer.
+    const char* where = "";  // the batch being built (for error messages)
     bool chk(const TPlan& tp, const Op& o, int ng, int ni, long long rows, long long cols) {
         if (!o.base || rows <= 0 || cols <= 0 || ng <= 0 || ni <= 0) return true;
         long long gmin = 0, gmax = ng - 1;
@@ -282,7 +284,17 @@ struct Red {
         const T* lo = o.base + gmin * o.gs + fmin * o.is;
         const T* hi = o.base + gmax * o.gs + fmax * o.is + (rows - 1) + (cols - 1) * o.ld + 1;
         if (!rs.has(lo, (size_t)(hi - lo) * sizeof(T))) {
-            fail("internal: a batch of the HODLR arithmetic points outside its buffers");
+            char m[512];
+            uintptr_t rlo = 0, rhi = 0;
+            const uintptr_t a = reinterpret_cast<uintptr_t>(lo);
+            for (const auto& q : rs.r)
+                if (q.first <= a) { rlo = q.first; rhi = q.second; }
+            snprintf(m, sizeof(m),
+                     "internal: a batch of the HODLR arithmetic points outside its buffers (%s: ng %d ni %d rows %lld "
+                     "cols %lld gs %lld is %lld ld %d map %d sh %d x %d; bytes [%#zx, %#zx) vs buffer [%#zx, %#zx))",
+                     where, ng, ni, rows, cols, o.gs, o.is, o.ld, o.map, o.sh, o.x, (size_t)a,
+                     (size_t)reinterpret_cast<uintptr_t>(hi), (size_t)rlo, (size_t)rhi);
+            fail(m);
             return false;
         }
         return true;
@@ -413,6 +425,7 @@ struct Red {
         std::vector<int*> rkd(L + 1, nullptr);
         for (int l = 1; l <= L; ++l)
             if (acc[l].R && hrecomp_smem_bytes(b >> l, acc[l].R, sizeof(T)) > 227 * 1024) return -2;
+        where = "truncate phase 1";
         TPlan p1;
         for (int l = 1; l <= L; ++l) {
             const int R = acc[l].R, s_ = b >> l;
@@ -472,6 +485,7 @@ struct Red {
                 for (int g = 0; g < nb; ++g)
                     for (int i = 0; i < (1 << l); ++i)
                         out.rank[(size_t)g * out.npb() + (1 << l) - 2 + i] = hr[l][((size_t)g << l) + i];
+        where = "truncate phase 2";
         TPlan p2;
         for (int l = 1; l <= L; ++l) {
             const int R = acc[l].R, Kl = Kn[l], s_ = b >> l;
@@ -539,6 +553,7 @@ struct Red {
         auto dU = [&](int l, long long is, int x = 0, int sh = 0) { return op(D.U[l], (long long)b * K[l], is, b, ms, sh, x); };
         auto dV = [&](int l, long long is, int x = 0, int sh = 0) { return op(D.V[l], (long long)b * K[l], is, b, ms, sh, x); };
         auto pan = [&](T* base, int Kk, long long is, int x = 0) { return op(base, (long long)b * Kk, is, b, -1, 0, x); };
+        where = "hinv leaves";
         // ---- leaf inverses (FP64) ----
         if (tri) {
             cudaStream_t st = s;
@@ -578,6 +593,7 @@ struct Red {
                     dQ[m] = get<T>(((size_t)nI << m) * K[m] * Kl);
                     if (!tP[m] || !dQ[m]) return fail("device allocation failed (HODLR inverse)");
                 }
+            where = "hinv stage 1";
             for (int m = l + 1; m <= L; ++m) {
                 if (!K[m]) continue;
                 const int Km = K[m], sm = b >> m;
@@ -590,6 +606,7 @@ struct Red {
                 tm(gd, pan(Yn[m], Km, sm), true, dV(l, sm), false, sm);
                 add(tp, gd);
             }
+            where = "hinv stage 2";
             GB gp = gb(nI, nl, leaf, Kl, pan(P[l], Kl, leaf));
             tm(gp, Gleaf, false, dU(l, leaf), false, leaf);
             GB gq = gb(nI, nl, leaf, Kl, pan(Q[l], Kl, leaf));
@@ -604,6 +621,7 @@ struct Red {
             }
             add(tp, gp);
             add(tp, gq);
+            where = "hinv cores";
             GB gc = gb(nI, 1 << l, Kl, Kl, op(Tc[l], (long long)(1 << l) * Kl * Kl, (long long)Kl * Kl, Kl));
             tm(gc, dV(l, s_), true, pan(P[l], Kl, s_), false, s_);
             add(tp, gc);
@@ -624,6 +642,7 @@ struct Red {
                     return e;
                 });
             }
+            where = "hinv new nodes";
             // per parent p: node a = 2p (rows 2p s), node c = 2p + 1 (rows 2p s + s)
             const int K2 = 2 * Kl, npar = 1 << (l - 1);
             const long long kg = (long long)npar * 4 * Kl * Kl, ki = 4LL * Kl * Kl, bg = (long long)b * Kl;
@@ -636,6 +655,7 @@ struct Red {
                 add(tp, g4);
             }
         }
+        where = "hinv assembly";
         // leaves absorb the pending updates; nodes gather [U'_l | Yn_{l-1} ..]
         {
             GB gf = gb(nI, nl, leaf, leaf, Gleaf);
@@ -745,6 +765,7 @@ struct Red {
         auto accU = [&](int l, int c, long long is = 0) { return op(acc[l].U + (size_t)c * b, (long long)b * acc[l].R, is, b); };
         auto accV = [&](int l, int c, long long is = 0) { return op(acc[l].V + (size_t)c * b, (long long)b * acc[l].R, is, b); };
         const Op Lleaf = op(Lo, bl, l2, leaf);
+        where = "hsum D";
         if (D) {
             const int md = tp.map(id);
             copy(tp, nO, 1, op(D->leaves, bl, 0, (int)bl, md), op(Lo, bl, 0, (int)bl), (int)bl, 1, alpha0);
@@ -758,11 +779,12 @@ struct Red {
         for (size_t t = 0; t < terms.size(); ++t) {
             const Term& x = terms[t];
             const HSet<T>& A = *x.A;
-            const int ma = tp.map(x.ia);
-            auto aU = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(A.U[l], (long long)b * A.K[l], is, b, ma, sh, x_); };
-            auto aV = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(A.V[l], (long long)b * A.K[l], is, b, ma, sh, x_); };
-            const Op aleaf = op(A.leaves, bl, l2, leaf, ma);
             if (x.kind == 1) {
+                const int ma = tp.map(x.ia);
+                auto aU = [&](int l, long long is) { return op(A.U[l], (long long)b * A.K[l], is, b, ma); };
+                auto aV = [&](int l, long long is) { return op(A.V[l], (long long)b * A.K[l], is, b, ma); };
+                const Op aleaf = op(A.leaves, bl, l2, leaf, ma);
+                where = "hsum scaled term";
                 const int mdl = tp.map(x.dlmap), mdr = tp.map(x.drmap);
                 const Op dlf = op(x.dl, b, leaf, 1, mdl), drf = op(x.dr, b, leaf, 1, mdr);
                 copy(tp, nO, nl, aleaf, Lleaf, leaf, leaf, x.alpha, T(1), &dlf, &drf);
@@ -776,7 +798,15 @@ struct Red {
                 continue;
             }
             const HSet<T>& B = *x.B;
-            const int mb = tp.map(x.ib);
+            where = "hsum product term";
+            // a term absent for a block is absent on both operands
+            std::vector<int> ian(x.ia), ibn(x.ib);
+            for (size_t g = 0; g < ian.size() && g < ibn.size(); ++g)
+                if (ian[g] < 0 || ibn[g] < 0) ian[g] = ibn[g] = -1;
+            const int ma2 = tp.map(ian), mb = tp.map(ibn);
+            auto aU = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(A.U[l], (long long)b * A.K[l], is, b, ma2, sh, x_); };
+            auto aV = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(A.V[l], (long long)b * A.K[l], is, b, ma2, sh, x_); };
+            const Op aleaf = op(A.leaves, bl, l2, leaf, ma2);
             auto bU = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(B.U[l], (long long)b * B.K[l], is, b, mb, sh, x_); };
             auto bV = [&](int l, long long is, int x_ = 0, int sh = 0) { return op(B.V[l], (long long)b * B.K[l], is, b, mb, sh, x_); };
             const Op bleaf = op(B.leaves, bl, l2, leaf, mb);
@@ -880,6 +910,7 @@ struct Red {
         const int nl = 1 << L;
         const long long bl = (long long)b * leaf, l2 = (long long)leaf * leaf;
         TPlan tp;
+        where = "hscale";
         const int ma = tp.map(ia), mdl = tp.map(dlmap), mdr = tp.map(drmap);
         const Op dlf = op(dl, b, leaf, 1, mdl), drf = op(dr, b, leaf, 1, mdr);
         copy(tp, nO, nl, op(A.leaves, bl, l2, leaf, ma), op(out.leaves, bl, l2, leaf), leaf, leaf, alpha, T(0), &dlf, &drf);
@@ -905,6 +936,7 @@ struct Red {
         const int nl = 1 << L;
         const long long bl = (long long)b * leaf, l2 = (long long)leaf * leaf;
         TPlan tp;
+        where = "hscale_into";
         const int ma = tp.map(ia), mdl = tp.map(dlmap), mdr = tp.map(drmap), mo = tp.map(ia_to_self(ia));
         const Op dlf = op(dl, b, leaf, 1, mdl), drf = op(dr, b, leaf, 1, mdr);
         copy(tp, nO, nl, op(A.leaves, bl, l2, leaf, ma), op(out.leaves, bl, l2, leaf, mo), leaf, leaf, alpha, T(0), &dlf,
@@ -936,6 +968,7 @@ struct Red {
         const int nq = (int)idx.size(), nl = 1 << L;
         std::vector<T*> tv(L + 1, nullptr);
         TPlan tp;
+        where = "happly";
         const int mh = tp.map(idx);
         const long long xg = (long long)b * nv, bl = (long long)b * leaf, l2 = (long long)leaf * leaf;
         for (int m = 1; m <= L; ++m) {
@@ -1008,6 +1041,7 @@ struct Red {
     // given (idx, base) groups.
     int expand(const HSet<T>& X, const std::vector<std::pair<std::vector<int>, T*>>& groups) {
         TPlan tp;
+        where = "expand";
         const int nl = 1 << L;
         const long long bb = (long long)b * b, bl = (long long)b * leaf, l2 = (long long)leaf * leaf;
         for (const auto& gr : groups) {
@@ -1169,7 +1203,7 @@ int reduce(Red<T>& R, int n, const double* Dband, const T* a, const T* c, int hm
                 t1.ia[k] = 2 * i;      // A_i XC_{(i-1)/2} = AC[2i] X[i]
                 t1.ib[k] = i;
                 t2.ia[k] = i + 1 < m ? 2 * i + 1 : -1;  // C_i XA_{(i+1)/2} = AC[2i+1] X[i+1]
-                t2.ib[k] = i + 1;
+                t2.ib[k] = i + 1 < m ? i + 1 : -1;
             }
             st = R.hsum(nk, T(1), D.get(), id, {t1, t2}, *Dn);
             if (st == -2) break;

@@ -511,7 +511,7 @@ void hcopy_chunks(int prob, long long elems, std::vector<int2>& chunks) {
 // ---------------------------------------------------------------- leaf inverses
 // FP64 inverse of every leaf of a tridiagonal block (level 0 of a 5-point
 // operator): leaf (g, lam) covers rows [lam leaf, (lam+1) leaf) of D_{sel[g]}
-// (Dband: [sub, diag, super] per block).  The leaf's LU factors (no pivoting:
+// (Dband: [sub, diag, super] per block, rounded to T first).  The leaf's LU factors (no pivoting:
 // used only for strictly diagonally dominant rows, where they are stable) are
 // formed once; thread c solves L y = e_c forward (y kept in shared memory,
 // ld leaf + 1) and U x = y backward, writing x over y; the leaf's inverse is
@@ -530,15 +530,19 @@ __global__ void __launch_bounds__(128) k_tri_leaf_inv(const double* __restrict__
     const double* sub = Dband + (size_t)sel[g] * 3 * b + (size_t)lam * leaf;
     const double* dia = sub + b;
     const double* sup = dia + b;
-    for (int r = threadIdx.x; r < leaf; r += blockDim.x) up[r] = sup[r];
+    // the entries as the factor's precision holds them (the off-diagonal
+    // nodes of the same blocks are stored in T): the leaf inverses are those
+    // of exactly the rounded blocks the rest of the arithmetic sees
+    auto rd = [](double v) { return (double)(T)v; };
+    for (int r = threadIdx.x; r < leaf; r += blockDim.x) up[r] = rd(sup[r]);
     if (threadIdx.x == 0) {
-        double u = dia[0];
+        double u = rd(dia[0]);
         dg[0] = u;
         lo[0] = 0.0;
         for (int r = 1; r < leaf; ++r) {
-            const double l = sub[r] / u;
+            const double l = rd(sub[r]) / u;
             lo[r] = l;
-            u = dia[r] - l * sup[r - 1];
+            u = rd(dia[r]) - l * rd(sup[r - 1]);
             dg[r] = u;
         }
     }

@@ -738,7 +738,7 @@ size_t node_svd_smem(int s, int k, int kz) {
 
 template <class T>
 int node_svd_kz(int s, int k) {  // widest work panel that fits in 200 KB
-    for (int kz = k; kz >= 8; kz /= 2)
+    for (int kz = k; kz >= std::min(8, k); kz /= 2)
         if (node_svd_smem<T>(s, k, kz) <= 200 * 1024) return kz;
     return 0;
 }

@@ -51,7 +51,9 @@ def host_resid(P, X, F):
 
 
 @pytest.mark.parametrize("idx,n,tol,leaf", [(0, 64, 1e-10, 16), (0, 128, 1e-8, 16), (1, 64, 1e-8, 16),
-                                            (1, 128, 1e-6, 32), (2, 128, 1e-6, 32), (2, 96, 1e-7, 16)])
+                                            (1, 128, 1e-6, 32), (2, 128, 1e-6, 32), (2, 96, 1e-7, 16),
+                                            (0, 64, 1e-10, 4), (1, 64, 1e-8, 8), (2, 128, 1e-8, 8),
+                                            (3, 64, 1e-10, 4)])
 def test_fp64_within_10_tol(lib, idx, n, tol, leaf):
     P = syn.make_config(idx, n)
     F = syn.rhs_uniform(P.N, 2, 2000 + idx)
