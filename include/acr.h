@@ -100,6 +100,12 @@ typedef struct {
                            the ranks stay small (at most ACR_HRANK_SWITCH);
                            k > 0: at most k levels; -1: none (every level dense,
                            compressed after the reduction) */
+    int h_sketch;       /* 1 (default): in HODLR arithmetic, a node whose summed
+                           factors are much wider than the operands' ranks is
+                           first truncated through a randomized range sketch
+                           (Rademacher test matrix, oversampling >= 6), with the
+                           exact truncation only where the sketch's rank comes
+                           within 6 of its width; 0: exact truncation only */
 } acr_opts;
 
 /* Largest off-diagonal rank of a level's blocks for which the automatic
@@ -193,6 +199,8 @@ typedef struct {
     double h_check[32];                  /* per level reduced in HODLR arithmetic (and the
                                             first level that failed it): the inverse check
                                             max_j ||D_j (D_j^-1 x) - x|| / ||x|| on random x */
+    long long h_nodes;                   /* node truncations in HODLR arithmetic */
+    long long h_sketch_redo;             /* of which the sketch left to the exact pass */
 } acr_stats_t;
 
 /* Copy the handle's statistics into *s. */

@@ -65,7 +65,7 @@ class acr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("input_kind", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_rank", ctypes.c_int), ("m_stop", ctypes.c_int), ("ir_tol", ctypes.c_double),
                 ("ir_max_iter", ctypes.c_int), ("stream", ctypes.c_void_p), ("refine", ctypes.c_int),
-                ("h_levels", ctypes.c_int)]
+                ("h_levels", ctypes.c_int), ("h_sketch", ctypes.c_int)]
 
 
 class acr_stats_t(ctypes.Structure):
@@ -83,7 +83,8 @@ class acr_stats_t(ctypes.Structure):
                 ("sweep_launches", ctypes.c_longlong), ("launches_factor", ctypes.c_longlong),
                 ("launches_solve", ctypes.c_longlong), ("compress_ms", ctypes.c_double),
                 ("h_levels", ctypes.c_int), ("h_ms", ctypes.c_double), ("h_flops", ctypes.c_double),
-                ("h_host_ms", ctypes.c_double), ("h_check", ctypes.c_double * 32)]
+                ("h_host_ms", ctypes.c_double), ("h_check", ctypes.c_double * 32),
+                ("h_nodes", ctypes.c_longlong), ("h_sketch_redo", ctypes.c_longlong)]
 
 
 def load(path: str = LIB_PATH):

@@ -201,6 +201,7 @@ void default_opts(acr_opts* o) {
     o->stream = nullptr;
     o->refine = ACR_REFINE_FGMRES;
     o->h_levels = 0;
+    o->h_sketch = 1;
 }
 
 // Level plan and persistent byte offsets.  Returns the arena size.  With
@@ -763,6 +764,7 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
             const double floor_es = sizeof(T) == 8 ? 32 * 2.220446049250313e-16 : 8 * 1.1920929e-7;
             hr->tol = std::max(h->tol / 10.0, floor_es);
             hr->kcap = h->opts.max_rank > 0 ? h->opts.max_rank : b;
+            hr->sketch = h->opts.h_sketch != 0;
             hr->rs.add(dD, (size_t)n * 3 * b * 8);
             hr->rs.add(aT, N * sizeof(T));
             hr->rs.add(cT, N * sizeof(T));
@@ -797,6 +799,8 @@ int run_factor(acr_ctx* h, const double* A, const double* D, const double* C) {
             h->st.h_levels = th;
             h->st.h_ms = h_ms;
             h->st.h_flops = hr->flops;
+            h->st.h_nodes = hr->nodes;
+            h->st.h_sketch_redo = hr->sketch_redo;
             h->st.launches_factor += launch_count() - hl0;
             if (th > 0) {
                 h->band0 = true;  // level 0 keeps A_i, C_i as diagonals

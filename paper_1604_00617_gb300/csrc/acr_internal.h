@@ -322,6 +322,10 @@ void hcopy_chunks(int prob, long long elems, std::vector<int2>& chunks);
 // (strictly diagonally dominant rows), written leaf after leaf to out
 template <class T>
 cudaError_t tri_leaf_inverse(const double* Dband, const int* sel, int nsel, int b, int leaf, T* out, cudaStream_t s);
+// gj_inverse for many small blocks: b <= 64 register resident (same pivoting
+// and info), larger b through gj_inverse
+template <class T>
+cudaError_t gj_inverse_small(T* mats, int b, int count, int* info, int* ws_piv, cudaStream_t s);
 template <class T>
 cudaError_t hkmat(const T* Tc, double* Kd, int nparent, int K, cudaStream_t s);
 template <class T>
@@ -377,6 +381,10 @@ template <class T>
 cudaError_t vgemm_t(const VPT<T>& P, cudaStream_t s);
 template <class T>
 cudaError_t hcopy_t(const CPT<T>& P, cudaStream_t s);
+// ks > 0 (and below min(s, R)): the randomized first pass with ks sketch
+// columns; rank -1 where it does not resolve the node, whose truncation then
+// needs the exact pass (hrecomp).  ks = 0: the exact pass.
 template <class T>
-cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, cudaStream_t st);
+cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, int ks, cudaStream_t st);
+size_t hrecomp_sketch_smem_bytes(int s, int R, int ks, int es);
 }  // namespace acr

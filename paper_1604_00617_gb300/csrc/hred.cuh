@@ -202,6 +202,9 @@ struct Red {
     std::vector<std::unique_ptr<HBuf>> tmp;  // temporaries of the current step
     double flops = 0.0;  // algorithmic flops of the products issued (2 M N K per term)
     bool oom = false;    // a device allocation was refused
+    bool sketch = true;  // randomized first truncation pass where a rank hint is given
+    long long nodes = 0;        // node truncations
+    long long sketch_redo = 0;  // nodes the sketch left to the exact pass
     // host time blocked on the device (uploads that wait for the stream,
     // synchronisations); the rest of the driver's wall time is host work
     double wait_ms = 0.0;
@@ -418,18 +421,54 @@ struct Red {
     // Truncates every node of every tree level (k_hrecomp), reads the ranks,
     // allocates `out` with the largest kept rank per tree level as capacity,
     // and writes U' = U (V^T V'), V' and the leaves (leaves_src: nb x b x leaf).
-    // Returns -2 (nothing done) when a level's panels exceed the truncation
-    // kernel's shared memory.
-    int truncate(const std::vector<Acc>& acc, int nb, const T* leaves_src, HSet<T>& out) {
+    // khint[l]: the rank expected at tree level l (the operands' ranks); with
+    // it, a level whose accumulated width is well above that rank is first
+    // truncated through a randomized sketch of width hint + 10 (rounded up
+    // to 8), and only the nodes the sketch does not resolve get the exact
+    // pass.  Returns -2 (nothing done) when a level's panels exceed the
+    // truncation kernel's shared memory.
+    int sync_wait(const char* msg) {
+        cudaError_t se;
+        {
+            WaitClock wc(wait_ms);
+            se = cudaStreamSynchronize(s);
+        }
+        if (se != cudaSuccess) {
+            cudaGetLastError();
+            return fail(msg);
+        }
+        return 0;
+    }
+    int read_ranks(const std::vector<int*>& rkd, int nb, std::vector<std::vector<int>>& hr) {
+        for (int l = 1; l <= L; ++l) {
+            if (!rkd[l]) continue;
+            hr[l].resize((size_t)nb << l);
+            if (cudaMemcpyAsync(hr[l].data(), rkd[l], hr[l].size() * sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+                return fail("rank readback failed");
+        }
+        return sync_wait("HODLR truncation failed on the device");
+    }
+    int truncate(const std::vector<Acc>& acc, int nb, const T* leaves_src, HSet<T>& out,
+                 const int* khint = nullptr) {
         std::vector<T*> vt(L + 1, nullptr);
         std::vector<int*> rkd(L + 1, nullptr);
-        for (int l = 1; l <= L; ++l)
-            if (acc[l].R && hrecomp_smem_bytes(b >> l, acc[l].R, sizeof(T)) > 227 * 1024) return -2;
+        std::vector<int> ksl(L + 1, 0);
+        for (int l = 1; l <= L; ++l) {
+            const int R = acc[l].R, s_ = b >> l;
+            if (R && hrecomp_smem_bytes(s_, R, sizeof(T)) > 227 * 1024) return -2;
+            if (R && khint && sketch) {
+                const int ks = std::max(16, (khint[l] + 10 + 7) / 8 * 8);
+                if (ks + 8 <= std::min(s_, R) && hrecomp_sketch_smem_bytes(s_, R, ks, sizeof(T)) <= 227 * 1024)
+                    ksl[l] = ks;
+            }
+        }
         where = "truncate phase 1";
         TPlan p1;
         for (int l = 1; l <= L; ++l) {
             const int R = acc[l].R, s_ = b >> l;
             if (R == 0) continue;
+            nodes += (long long)nb << l;
             vt[l] = get<T>((size_t)nb * b * R);
             rkd[l] = get<int>((size_t)nb << l);
             if (!vt[l] || !rkd[l]) return fail("device allocation failed (HODLR truncation)");
@@ -441,7 +480,7 @@ struct Red {
             chk(p1, Vo, nb, 1 << l, s_, R);
             int* rr = rkd[l];
             const double tl = tol;
-            const int kc = kcap;
+            const int kc = kcap, ks = ksl[l];
             cudaStream_t st = s;
             const TPlan* tpp = &p1;
             fn(p1, [=](const unsigned char* d) {
@@ -451,26 +490,56 @@ struct Red {
                 Q.V = resolve(V, *tpp, d);
                 Q.Vout = resolve(Vo, *tpp, d);
                 Q.s = s_; Q.R = R; Q.wout = R; Q.ni = 1 << l; Q.ng = nb;
-                return hrecomp_t<T>(Q, rr, tl, kc, st);
+                return hrecomp_t<T>(Q, rr, tl, kc, ks, st);
             });
         }
         if (run(p1)) return -1;
         std::vector<std::vector<int>> hr(L + 1);
+        if (read_ranks(rkd, nb, hr)) return -1;
+        // the nodes the sketch left open: the exact pass, as one list
+        std::vector<RProb<T>> redo;
+        std::vector<std::pair<int, size_t>> where_;
+        int smax = 0, Rmax = 0;
         for (int l = 1; l <= L; ++l) {
-            if (!rkd[l]) continue;
-            hr[l].resize((size_t)nb << l);
-            if (cudaMemcpyAsync(hr[l].data(), rkd[l], hr[l].size() * sizeof(int), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess)
+            if (!ksl[l]) continue;
+            const int R = acc[l].R, s_ = b >> l;
+            for (size_t e = 0; e < hr[l].size(); ++e) {
+                if (hr[l][e] >= 0) continue;
+                const size_t g = e >> l;
+                const int i = (int)(e & ((1u << l) - 1));
+                const size_t base = g * b * R;
+                RProb<T> q;
+                q.U = acc[l].U + base + (size_t)i * s_;
+                q.V = acc[l].V + base + (size_t)(i ^ 1) * s_;
+                q.Vout = vt[l] + base + (size_t)(i ^ 1) * s_;
+                q.ldu = q.ldv = q.ldvo = b;
+                q.s = s_; q.R = R; q.wout = R;
+                redo.push_back(q);
+                where_.push_back({l, e});
+                smax = std::max(smax, s_);
+                Rmax = std::max(Rmax, R);
+            }
+        }
+        if (!redo.empty()) {
+            where = "truncate exact pass";
+            sketch_redo += (long long)redo.size();
+            int* rk2 = get<int>(redo.size());
+            if (!rk2) return fail("device allocation failed (HODLR truncation)");
+            TPlan pr;
+            const size_t off = pr.pl.put(redo.data(), redo.size() * sizeof(RProb<T>));
+            const int n = (int)redo.size();
+            const double tl = tol;
+            const int kc = kcap;
+            cudaStream_t st = s;
+            fn(pr, [=](const unsigned char* d) {
+                return hrecomp<T>(reinterpret_cast<const RProb<T>*>(d + off), n, smax, Rmax, rk2, tl, kc, st);
+            });
+            if (run(pr)) return -1;
+            std::vector<int> r2(redo.size());
+            if (cudaMemcpyAsync(r2.data(), rk2, r2.size() * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
                 return fail("rank readback failed");
-        }
-        cudaError_t se;
-        {
-            WaitClock wc(wait_ms);
-            se = cudaStreamSynchronize(s);
-        }
-        if (se != cudaSuccess) {
-            cudaGetLastError();
-            return fail("HODLR truncation failed on the device");
+            if (sync_wait("HODLR truncation failed on the device")) return -1;
+            for (size_t j = 0; j < redo.size(); ++j) hr[where_[j].first][where_[j].second] = r2[j];
         }
         int Kn[HMAXL + 1] = {0};
         for (int l = 1; l <= L; ++l)
@@ -574,7 +643,7 @@ struct Red {
                     e = convert_f2d(reinterpret_cast<const float*>(Gl), Ld, (long long)nI * bl, st);
                     if (e != cudaSuccess) return e;
                 }
-                e = gj_inverse<double>(Ld, lf, nI * nl, info, piv, st);
+                e = gj_inverse_small<double>(Ld, lf, nI * nl, info, piv, st);
                 if (e != cudaSuccess) return e;
                 if (sizeof(T) == 4) e = convert_d2f(Ld, reinterpret_cast<float*>(Gl), (long long)nI * bl, st);
                 return e;
@@ -635,7 +704,7 @@ struct Red {
                 fn(tp, [=](const unsigned char*) -> cudaError_t {
                     cudaError_t e = hkmat<T>(tc, kd, (int)np, Kl, st);
                     if (e != cudaSuccess) return e;
-                    e = gj_inverse<double>(kd, 2 * Kl, (int)np, ik, piv, st);
+                    e = gj_inverse_small<double>(kd, 2 * Kl, (int)np, ik, piv, st);
                     if (e != cudaSuccess) return e;
                     if (sizeof(T) == 4)
                         e = convert_d2f(kd, reinterpret_cast<float*>(kt), (long long)np * 4 * Kl * Kl, st);
@@ -685,7 +754,7 @@ struct Red {
             }
         }
         if (run(tp)) return -1;
-        if (const int tr = truncate(acc, nI, Gl, out)) return tr;
+        if (const int tr = truncate(acc, nI, Gl, out, D.K)) return tr;
         std::vector<int> hi(ninfo);
         if (cudaMemcpy(hi.data(), info, ninfo * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail("pivot readback failed");
@@ -895,7 +964,15 @@ struct Red {
             add(tp, g5);
         }
         if (run(tp)) return -1;
-        return truncate(acc, nO, Lo, out);
+        int hint[HMAXL + 1] = {0};
+        for (int l = 1; l <= L; ++l) {
+            if (D) hint[l] = D->K[l];
+            for (const Term& x : terms) {
+                hint[l] = std::max(hint[l], x.A->K[l]);
+                if (x.kind != 1) hint[l] = std::max(hint[l], x.B->K[l]);
+            }
+        }
+        return truncate(acc, nO, Lo, out, hint);
     }
 
     // out (nO blocks) = alpha diag(dl) A[ia] diag(dr): ranks unchanged, no

@@ -271,53 +271,154 @@ size_t hrecomp_smem(int s, int R) {
            (size_t)ke * sizeof(int) + 16;
 }
 
+// Sketch mode (ks > 0): the range of U V^T is first captured by the sketch
+// Y = U (V^T Omega) with ks Rademacher columns (a fixed hash of row and
+// column), Y = Q R; then B^T = V (U^T Q) (s x ks) plays the part of Y below,
+// so every QR and the Jacobi run at width ks instead of min(s, R).  A node
+// whose kept rank exceeds ks - 6 is not resolved by the sketch: its rank is
+// reported as -1 and nothing is written (the exact mode is run on it).
+
 template <class T>
-__device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T tol, int kcap) {
+size_t hrecomp_sk_smem(int s, int R, int ks) {
+    return ((size_t)s * R + (size_t)R * ks + 2 * (size_t)s * ks + (size_t)ks * ks + (size_t)s * HR_KZ +
+            3 * (size_t)ks) * sizeof(T) + (size_t)ks * sizeof(int) + 16;
+}
+
+__device__ __forceinline__ float rademacher(int r, int c) {
+    uint32_t h = (uint32_t)r * 0x9E3779B1u + (uint32_t)c * 0x7FEB352Du + 0x165667B1u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return (h & 1u) ? 1.f : -1.f;
+}
+
+template <class T>
+__device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T tol, int kcap, int ks = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[9];
     __shared__ int s_flag;
-    const int s = Pr.s, R = Pr.R, r0 = min(s, R), ke = r0 + (r0 & 1);
+    const bool sk = ks > 0;
+    const int s = Pr.s, R = Pr.R, r0 = sk ? min(ks, min(s, R)) : min(s, R), ke = r0 + (r0 & 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T* Pn = reinterpret_cast<T*>(smem_raw);
-    T* RU = Pn + (size_t)s * R;
-    T* RY = RU + (size_t)r0 * R;
+    T *RU, *Wk = nullptr, *Yp = nullptr, *Qp = nullptr, *RY;
+    if (!sk) {
+        RU = Pn + (size_t)s * R;
+        RY = RU + (size_t)r0 * R;
+    } else {
+        RU = nullptr;
+        Wk = Pn + (size_t)s * R;
+        Yp = Wk + (size_t)R * ks;
+        Qp = Yp + (size_t)s * ks;
+        RY = Qp + (size_t)s * ks;
+    }
     T* Z = RY + (size_t)ke * ke;
     T* tau = Z + (size_t)s * HR_KZ;
     T* rdg = tau + ke;
     T* sv = rdg + ke;
     int* ord = reinterpret_cast<int*>(sv + ke);
+    T* Yr = sk ? Yp : Pn;  // the panel whose QR feeds the Jacobi step
     const int wout = Pr.wout;
     if (r0 == 0) {
         for (int e = tid; e < s * wout; e += 256) Pr.Vout[(size_t)(e % s) + (size_t)(e / s) * Pr.ldvo] = T(0);
         if (tid == 0) *rank_out = 0;
         return;
     }
-    // ---- QR of U: keep R_U (r0 x R, upper trapezoidal) -----------------------
-    for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.U[(size_t)(e % s) + (size_t)(e / s) * Pr.ldu];
-    __syncthreads();
-    hh_qr<T>(Pn, s, R, tau, rdg, red, &s_flag);
-    for (int e = tid; e < r0 * R; e += 256) {
-        const int i = e % r0, j = e / r0;
-        RU[e] = (i < j) ? Pn[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
-    }
-    __syncthreads();
-    // ---- Y = V R_U^T in the panel (column c reads V's columns >= c only, so
-    // increasing c may overwrite column c in place; each thread owns its rows)
-    for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
-    __syncthreads();
-    for (int r = tid; r < s; r += 256)
-        for (int c = 0; c < r0; ++c) {
-            T y = T(0);
-            for (int j = c; j < R; ++j) y = fma(Pn[r + (size_t)j * s], RU[c + (size_t)j * r0], y);
-            Pn[r + (size_t)c * s] = y;
+    if (sk) {
+        const int k = r0;
+        for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
+        __syncthreads();
+        for (int e = tid; e < R * k; e += 256) {  // Wk = V^T Omega
+            const int j = e % R, c = e / R;
+            T acc = T(0);
+            for (int r = 0; r < s; ++r) acc = fma(Pn[r + (size_t)j * s], (T)rademacher(r, c), acc);
+            Wk[e] = acc;
         }
-    __syncthreads();
+        __syncthreads();
+        for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.U[(size_t)(e % s) + (size_t)(e / s) * Pr.ldu];
+        __syncthreads();
+        for (int e = tid; e < s * k; e += 256) {  // Y = U Wk
+            const int r = e % s, c = e / s;
+            T acc = T(0);
+            for (int j = 0; j < R; ++j) acc = fma(Pn[r + (size_t)j * s], Wk[j + (size_t)c * R], acc);
+            Yp[e] = acc;
+        }
+        __syncthreads();
+        hh_qr<T>(Yp, s, k, tau, rdg, red, &s_flag);
+        for (int e = tid; e < s * k; e += 256) Qp[e] = ((e % s) == (e / s)) ? T(1) : T(0);
+        __syncthreads();
+        for (int j = k - 1; j >= 0; --j) {  // Q = H_0 .. H_{k-1} [I; 0]
+            const T tj = tau[j];
+            if (tj == T(0)) continue;
+            const T* v = Yp + (size_t)j * s;
+            for (int c = warp; c < k; c += 8) {
+                T* qc = Qp + (size_t)c * s;
+                T d = T(0);
+                for (int r = j + lane; r < s; r += 32) d += v[r] * qc[r];
+                d = hwarp_sum(d) * tj;
+                for (int r = j + lane; r < s; r += 32) qc[r] -= d * v[r];
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < R * k; e += 256) {  // Wk = U^T Q
+            const int j = e % R, c = e / R;
+            T acc = T(0);
+            for (int r = 0; r < s; ++r) acc = fma(Pn[r + (size_t)j * s], Qp[r + (size_t)c * s], acc);
+            Wk[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
+        __syncthreads();
+        for (int e = tid; e < s * k; e += 256) {  // B^T = V Wk
+            const int r = e % s, c = e / s;
+            T acc = T(0);
+            for (int j = 0; j < R; ++j) acc = fma(Pn[r + (size_t)j * s], Wk[j + (size_t)c * R], acc);
+            Yp[e] = acc;
+        }
+        __syncthreads();
+    } else if (R >= s) {
+        // ---- as wide as the node: Y = V U^T (s x s) directly -------------------
+        // (U V^T = Y^T; Y's left singular vectors are those wanted), one QR
+        // instead of two
+        for (int e = tid; e < s * s; e += 256) {
+            const int r = e % s, c = e / s;
+            T y = T(0);
+            for (int j = 0; j < R; ++j)
+                y = fma(Pr.V[(size_t)r + (size_t)j * Pr.ldv], Pr.U[(size_t)c + (size_t)j * Pr.ldu], y);
+            Pn[e] = y;
+        }
+        __syncthreads();
+    } else {
+        // ---- QR of U: keep R_U (r0 x R, upper trapezoidal) -------------------
+        for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.U[(size_t)(e % s) + (size_t)(e / s) * Pr.ldu];
+        __syncthreads();
+        hh_qr<T>(Pn, s, R, tau, rdg, red, &s_flag);
+        for (int e = tid; e < r0 * R; e += 256) {
+            const int i = e % r0, j = e / r0;
+            RU[e] = (i < j) ? Pn[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
+        }
+        __syncthreads();
+        // ---- Y = V R_U^T in the panel (column c reads V's columns >= c only,
+        // so increasing c may overwrite column c in place; each thread owns its
+        // rows)
+        for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
+        __syncthreads();
+        for (int r = tid; r < s; r += 256)
+            for (int c = 0; c < r0; ++c) {
+                T y = T(0);
+                for (int j = c; j < R; ++j) y = fma(Pn[r + (size_t)j * s], RU[c + (size_t)j * r0], y);
+                Pn[r + (size_t)c * s] = y;
+            }
+        __syncthreads();
+    }
     // ---- QR of Y (s x r0): R_Y into RY (ke x ke, zero padded) ----------------
-    hh_qr<T>(Pn, s, r0, tau, rdg, red, &s_flag);
+    hh_qr<T>(Yr, s, r0, tau, rdg, red, &s_flag);
     for (int e = tid; e < ke * ke; e += 256) {
         const int i = e % ke, j = e / ke;
         T v = T(0);
-        if (i < r0 && j < r0) v = (i < j) ? Pn[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
+        if (i < r0 && j < r0) v = (i < j) ? Yr[i + (size_t)j * s] : (i == j ? rdg[i] : T(0));
         RY[e] = v;
     }
     __syncthreads();
@@ -338,24 +439,53 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
     }
     const T negl = red[8] * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
     __syncthreads();
+    // Squared column norms are kept in sv (recomputed each sweep, updated by
+    // every rotation: ||a'||^2 = ||a||^2 - t g, ||b'||^2 = ||b||^2 + t g).  A
+    // pair whose two columns are both below 1e-2 tol times the largest
+    // initial column norm (a lower bound of sigma_1) is left alone: whatever
+    // the rotations do, those columns stay far below the truncation level,
+    // so they cannot change the kept singular values or the rank.
+    T* cn = sv;
+    for (int c = warp; c < ke; c += 8) {
+        T n2 = T(0);
+        for (int r = lane; r < ke; r += 32) n2 += RY[r + (size_t)c * ke] * RY[r + (size_t)c * ke];
+        n2 = hwarp_sum(n2);
+        if (lane == 0) cn[c] = n2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        T mx = T(0);
+        for (int c = 0; c < ke; ++c) mx = fmax(mx, cn[c]);
+        red[8] = fmax(negl, mx * (T(1e-2) * tol) * (T(1e-2) * tol));
+    }
+    __syncthreads();
+    const T skip2 = red[8];
+    __syncthreads();
     if (ke >= 2) {
         for (int sweep = 0; sweep < 16; ++sweep) {
             if (tid == 0) s_flag = 0;
+            if (sweep > 0) {
+                for (int c = warp; c < ke; c += 8) {
+                    T n2 = T(0);
+                    for (int r = lane; r < ke; r += 32) n2 += RY[r + (size_t)c * ke] * RY[r + (size_t)c * ke];
+                    n2 = hwarp_sum(n2);
+                    if (lane == 0) cn[c] = n2;
+                }
+            }
             __syncthreads();
             for (int rnd = 0; rnd < ke - 1; ++rnd) {
                 for (int q = warp; q < ke / 2; q += 8) {
                     int a, bc;
                     if (q == 0) { a = ke - 1; bc = rnd; }
                     else { a = (rnd + q) % (ke - 1); bc = (rnd - q + (ke - 1)) % (ke - 1); }
+                    const T al = cn[a], be = cn[bc];
+                    if (!(al + be > skip2)) continue;  // uniform over the warp
                     T* ca = RY + (size_t)a * ke;
                     T* cb = RY + (size_t)bc * ke;
-                    T al = T(0), be = T(0), ga = T(0);
-                    for (int r = lane; r < ke; r += 32) {
-                        const T x = ca[r], y = cb[r];
-                        al += x * x; be += y * y; ga += x * y;
-                    }
-                    al = hwarp_sum(al); be = hwarp_sum(be); ga = hwarp_sum(ga);
-                    if (al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                    T ga = T(0);
+                    for (int r = lane; r < ke; r += 32) ga += ca[r] * cb[r];
+                    ga = hwarp_sum(ga);
+                    if (fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
                         const T zeta = (be - al) / (T(2) * ga);
                         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                         const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
@@ -364,7 +494,12 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
                             ca[r] = cs * x - sn * y;
                             cb[r] = sn * x + cs * y;
                         }
-                        if (lane == 0) s_flag = 1;
+                        __syncwarp();
+                        if (lane == 0) {
+                            cn[a] = fmax(T(0), al - t * ga);
+                            cn[bc] = be + t * ga;
+                            s_flag = 1;
+                        }
                     }
                 }
                 __syncthreads();
@@ -397,11 +532,13 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
         int r = 0;
         if (s1 > T(0) && !isnan(s1))
             while (r < ke && r < wout && r < kcap && sv[ord[r]] > tol * s1) ++r;
+        if (sk && r > r0 - 6 && r < kcap && r0 < min(s, R)) r = -1;  // the sketch saturated
         s_flag = r;
         *rank_out = r;
     }
     __syncthreads();
     const int rk = s_flag;
+    if (rk < 0) return;
     // ---- V' = Q_Y [W; 0] for the kept columns, HR_KZ at a time -----------------
     for (int c0 = 0; c0 < wout; c0 += HR_KZ) {
         const int nc = min(HR_KZ, wout - c0);
@@ -420,7 +557,7 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
             for (int j = r0 - 1; j >= 0; --j) {
                 const T tj = tau[j];
                 if (tj == T(0)) continue;
-                const T* v = Pn + (size_t)j * s;
+                const T* v = Yr + (size_t)j * s;
                 for (int c = warp; c < nc; c += 8) {
                     T* zc = Z + (size_t)c * s;
                     T d = T(0);
@@ -464,6 +601,10 @@ cudaError_t hrecomp(const RProb<T>* probs, int nprob, int smax, int Rmax, int* r
 
 size_t hrecomp_smem_bytes(int s, int R, int es) {
     return es == 8 ? hrecomp_smem<double>(s, R) : hrecomp_smem<float>(s, R);
+}
+
+size_t hrecomp_sketch_smem_bytes(int s, int R, int ks, int es) {
+    return es == 8 ? hrecomp_sk_smem<double>(s, R, ks) : hrecomp_sk_smem<float>(s, R, ks);
 }
 
 // ---------------------------------------------------------------- k_hcopy
@@ -761,6 +902,7 @@ __global__ void __launch_bounds__(256) k_vgemm_t(const __grid_constant__ VPT<T> 
         for (int k0 = 0; k0 < Tm.K; k0 += VG_BK) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                if (!ta && 4 * q >= Tm.K - k0) break;  // columns the multiply loop does not read
                 const int e = tid + 256 * q;
                 int mm, kk;
                 if (!ta) { mm = e & 63; kk = e >> 6; }
@@ -780,14 +922,22 @@ __global__ void __launch_bounds__(256) k_vgemm_t(const __grid_constant__ VPT<T> 
                 Bs[kk][nn] = v;
             }
             __syncthreads();
+            // terms of small inner dimension (node ranks) use only the first
+            // K - k0 staged columns: stop after them, in steps of 4
+            const int kn = min(VG_BK, Tm.K - k0);
 #pragma unroll
-            for (int kk = 0; kk < VG_BK; ++kk) {
-                const T b0 = Bs[kk][2 * ty], b1 = Bs[kk][2 * ty + 1];
+            for (int k4 = 0; k4 < VG_BK; k4 += 4) {
+                if (k4 >= kn) break;
 #pragma unroll
-                for (int r = 0; r < RI; ++r) {
-                    const T a = As[kk][tx + (NARROW ? 0 : 16 * r)];
-                    acc[r][0] = fma(a, b0, acc[r][0]);
-                    acc[r][1] = fma(a, b1, acc[r][1]);
+                for (int kq = 0; kq < 4; ++kq) {
+                    const int kk = k4 + kq;
+                    const T b0 = Bs[kk][2 * ty], b1 = Bs[kk][2 * ty + 1];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const T a = As[kk][tx + (NARROW ? 0 : 16 * r)];
+                        acc[r][0] = fma(a, b0, acc[r][0]);
+                        acc[r][1] = fma(a, b1, acc[r][1]);
+                    }
                 }
             }
             __syncthreads();
@@ -863,7 +1013,7 @@ cudaError_t hcopy_t(const CPT<T>& P, cudaStream_t s) {
 // one node per CTA; the body is k_hrecomp's
 template <class T>
 __global__ void __launch_bounds__(256) k_hrecomp_t(const __grid_constant__ RPT<T> P, int* __restrict__ ranks, T tol,
-                                                   int kcap) {
+                                                   int kcap, int ks) {
     const int node = blockIdx.x;
     const int g = node / P.ni, i = node - g * P.ni;
     RProb<T> q;
@@ -876,19 +1026,20 @@ __global__ void __launch_bounds__(256) k_hrecomp_t(const __grid_constant__ RPT<T
     q.s = P.s;
     q.R = P.R;
     q.wout = P.wout;
-    hrecomp_body<T>(q, ranks + node, tol, kcap);
+    hrecomp_body<T>(q, ranks + node, tol, kcap, ks);
 }
 
 template <class T>
-cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, cudaStream_t st) {
+cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, int ks_, cudaStream_t st) {
     const long long n = (long long)P.ng * P.ni;
     if (n <= 0) return cudaSuccess;
     if (n >= (1LL << 31)) return cudaErrorInvalidValue;
-    const size_t sm = hrecomp_smem<T>(P.s, P.R);
+    const int ks = (ks_ > 0 && ks_ < std::min(P.s, P.R)) ? ks_ : 0;
+    const size_t sm = ks ? hrecomp_sk_smem<T>(P.s, P.R, ks) : hrecomp_smem<T>(P.s, P.R);
     if (sm > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem((const void*)k_hrecomp_t<T>, sm);
     if (e != cudaSuccess) return e;
-    k_hrecomp_t<T><<<(unsigned)n, 256, sm, st>>>(P, ranks, (T)tol, kcap);
+    k_hrecomp_t<T><<<(unsigned)n, 256, sm, st>>>(P, ranks, (T)tol, kcap, ks);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -897,7 +1048,185 @@ template cudaError_t vgemm_t<float>(const VPT<float>&, cudaStream_t);
 template cudaError_t vgemm_t<double>(const VPT<double>&, cudaStream_t);
 template cudaError_t hcopy_t<float>(const CPT<float>&, cudaStream_t);
 template cudaError_t hcopy_t<double>(const CPT<double>&, cudaStream_t);
-template cudaError_t hrecomp_t<float>(const RPT<float>&, int*, double, int, cudaStream_t);
-template cudaError_t hrecomp_t<double>(const RPT<double>&, int*, double, int, cudaStream_t);
+template cudaError_t hrecomp_t<float>(const RPT<float>&, int*, double, int, int, cudaStream_t);
+template cudaError_t hrecomp_t<double>(const RPT<double>&, int*, double, int, int, cudaStream_t);
+
+}  // namespace acr
+
+// =============================================================================
+// Batched inversion of small blocks (b <= 64) by Gauss-Jordan with partial
+// pivoting, register resident: 256 threads per block, thread (r, g) = (tid &
+// 63, tid >> 6) holds row r, columns [16 g, 16 g + 16) of the 64 x 64 working
+// matrix (a b x b block is embedded in the identity).  Each pivot step finds
+// the pivot in column k (lowest row index on ties), swaps rows k and p, and
+// broadcasts the scaled pivot row and column k through shared memory for the
+// rank-1 update; column k of the result is -column k / pivot and the pivot
+// position its reciprocal.  The composed row interchanges are undone on the
+// columns at the end.  info[e] = k + 1 for the first pivot k that is not
+// finite or at most 16 eps(T) max |block| in magnitude (0: none).
+// =============================================================================
+namespace acr {
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gj_reg(T* __restrict__ mats, int b, int* __restrict__ info) {
+    constexpr int B = 64, G = 16;
+    __shared__ T rowk[B], colk[B], rowp[B];
+    __shared__ T wv[8];
+    __shared__ int wi[8];
+    __shared__ int piv[B], srcpos[B], dstpos[B];
+    __shared__ int s_info, s_p;
+    __shared__ T s_amax;
+    const int tid = threadIdx.x, r = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
+    T* Gm = mats + (size_t)blockIdx.x * b * b;
+    T m[G];
+    T amax = T(0);
+    bool fin = true;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        const int c = g * G + j;
+        T v;
+        if (r < b && c < b) {
+            v = Gm[(size_t)r + (size_t)c * b];
+            fin &= isfinite(v);
+            amax = fmax(amax, fabs(v));
+        } else {
+            v = (r == c) ? T(1) : T(0);
+        }
+        m[j] = v;
+    }
+    if (!fin) amax = T(INFINITY);
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) wv[warp] = amax;
+    if (tid == 0) s_info = 0;
+    __syncthreads();
+    if (tid == 0) {
+        T a = T(0);
+        for (int w = 0; w < 8; ++w) a = fmax(a, wv[w]);
+        s_amax = a;
+    }
+    __syncthreads();
+    const T tiny = T(16) * (sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-7)) * s_amax;
+    for (int k = 0; k < b; ++k) {
+        const int gk = k >> 4, jk = k & 15;
+        // ---- pivot: the two warps holding column k reduce over rows >= k ----
+        if (g == gk) {
+            T v = T(-1);
+            int idx = 0x7fffffff;
+            T mk = T(0);
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (j == jk) mk = m[j];  // register select (no dynamic index)
+            if (r >= k && r < b) {
+                v = fabs(mk);
+                if (!isfinite(mk)) v = T(INFINITY);
+                idx = r;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+            }
+            if (lane == 0) { wv[warp & 1] = v; wi[warp & 1] = idx; }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            T v = wv[0];
+            int idx = wi[0];
+            if (wv[1] > v || (wv[1] == v && wi[1] < idx)) { v = wv[1]; idx = wi[1]; }
+            const int p = (idx < b) ? idx : k;
+            s_p = p;
+            piv[k] = p;
+            if ((!(v > tiny) || !isfinite(v)) && s_info == 0) s_info = k + 1;
+        }
+        __syncthreads();
+        const int p = s_p;
+        // ---- interchange rows k and p ----
+        if (p != k) {
+            if (r == k) {
+#pragma unroll
+                for (int j = 0; j < G; ++j) rowk[g * G + j] = m[j];
+            } else if (r == p) {
+#pragma unroll
+                for (int j = 0; j < G; ++j) rowp[g * G + j] = m[j];
+            }
+            __syncthreads();
+            if (r == k) {
+#pragma unroll
+                for (int j = 0; j < G; ++j) m[j] = rowp[g * G + j];
+            } else if (r == p) {
+#pragma unroll
+                for (int j = 0; j < G; ++j) m[j] = rowk[g * G + j];
+            }
+            __syncthreads();
+        }
+        // ---- pivot row and column to shared memory ----
+        if (g == gk) {
+            T mk = T(0);
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (j == jk) mk = m[j];
+            colk[r] = mk;
+        }
+        if (r == k) {
+#pragma unroll
+            for (int j = 0; j < G; ++j) rowk[g * G + j] = m[j];
+        }
+        __syncthreads();
+        const T pv = rowk[k];
+        const bool bad = !(fabs(pv) > tiny) || !isfinite(pv);
+        const T inv = bad ? T(1) : T(1) / pv;
+        // ---- update ----
+        if (r == k) {
+#pragma unroll
+            for (int j = 0; j < G; ++j) m[j] = (g * G + j == k) ? inv : m[j] * inv;
+        } else {
+            const T ck = colk[r];
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int c = g * G + j;
+                m[j] = (c == k) ? -ck * inv : fma(-ck * inv, rowk[c], m[j]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- undo the interchanges on the columns (composed from the pivots in
+    // reverse order) ----
+    if (tid == 0) {
+        for (int c = 0; c < B; ++c) srcpos[c] = c;
+        for (int k = b - 1; k >= 0; --k) {
+            const int pk = piv[k];
+            const int t = srcpos[k]; srcpos[k] = srcpos[pk]; srcpos[pk] = t;
+        }
+        // srcpos[c]: the working column that holds output column c
+        for (int c = 0; c < B; ++c) dstpos[srcpos[c]] = c;
+        info[blockIdx.x] = s_info;
+    }
+    __syncthreads();
+    if (r < b) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const int src = g * G + j;
+            if (src < b) Gm[(size_t)r + (size_t)dstpos[src] * b] = m[j];
+        }
+    }
+}
+
+// The same inversion for b > 64 falls back to gj_inverse.
+template <class T>
+cudaError_t gj_inverse_small(T* mats, int b, int count, int* info, int* ws_piv, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (b > 64) return gj_inverse<T>(mats, b, count, info, ws_piv, s);
+    long long done = 0;
+    while (done < count) {
+        const int cnt = (int)std::min<long long>(count - done, 1 << 30);
+        k_gj_reg<T><<<cnt, 256, 0, s>>>(mats + (size_t)done * b * b, b, info + done);
+        count_launches(1);
+        done += cnt;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t gj_inverse_small<float>(float*, int, int, int*, int*, cudaStream_t);
+template cudaError_t gj_inverse_small<double>(double*, int, int, int*, int*, cudaStream_t);
 
 }  // namespace acr
