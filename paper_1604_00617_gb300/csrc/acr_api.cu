@@ -1697,10 +1697,13 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
     } else {
         // restarted FGMRES(m), right preconditioned, one Krylov space per column
         const int m = std::min(ACR_FGMRES_RESTART, maxit);
-        DevBuf V, Z, hacc;
+        DevBuf V, Z, hacc, sq2, hsb, needb;
         CK(V.alloc((size_t)(m + 1) * NQ * 8, s));
         CK(Z.alloc((size_t)m * NQ * 8, s));
         CK(hacc.alloc((size_t)(m + 1) * nrhs * 8, s));
+        CK(sq2.alloc((size_t)64 * nrhs * 8, s));
+        CK(hsb.alloc((size_t)nrhs * 8, s));
+        CK(needb.alloc((size_t)nrhs * sizeof(int), s));
         double* Vp = V.as<double>();
         double* Zp = Z.as<double>();
         std::vector<double> H((size_t)nrhs * (m + 1) * m), g((size_t)nrhs * (m + 1)), cs((size_t)nrhs * m),
@@ -1727,16 +1730,33 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
                 ++iters;
                 if ((st = op.mv(Zj))) return st;
                 double* w = wb.as<double>();
-                // classical Gram-Schmidt, twice; the coefficients stay on the
-                // device and column j of H (h1 + h2) comes back with the norm
-                for (int pass = 0; pass < 2; ++pass) {
-                    CK(multi_dot(Vp, j + 1, w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
-                    CK(gs_coef(sq.as<double>(), coef.as<double>(), hacc.as<double>(), (j + 1) * nrhs, pass == 0, s));
-                    CK(multi_axpy(w, Vp, j + 1, coef.as<double>(), N, nrhs, s));
+                // classical Gram-Schmidt: h1 = V^T w with |w|^2 in one read of
+                // V, w -= V h1 with |w'|^2 in a second.  A column repeats the
+                // pass (h2 = V^T w', w' -= V h2, decided on the device) only
+                // where the first cancelled the norm below 1e-2 |w|: a pass
+                // leaves w' off orthogonal by about u |w| / |w'|, so above
+                // that ratio the basis stays orthogonal to ~1e-12, well
+                // within the refinement targets.  Column j of H (h1 [+ h2])
+                // comes back with the final norm.
+                const int nv = j + 1;
+                double* sqp = sq.as<double>();
+                double* sq2p = sq2.as<double>();
+                CK(multi_dot_self(Vp, nv, w, N, nrhs, ws.as<double>(), sqp, s));
+                CK(gs_coef(sqp, coef.as<double>(), hacc.as<double>(), nv * nrhs, true, s));
+                CK(gs_update_norm(w, Vp, nv, coef.as<double>(), N, nrhs, nullptr, ws.as<double>(),
+                                  sq2p + (size_t)63 * nrhs, s));
+                if (N <= 4LL * 1024 * 1024) {
+                    CK(gs_reorth(w, Vp, nv, sqp + (size_t)nv * nrhs, sq2p + (size_t)63 * nrhs, 1e-4, sq2p,
+                                 coef.as<double>(), hacc.as<double>(), needb.as<int>(), hsb.as<double>(), N, nrhs,
+                                 ws.as<double>(), s));
+                } else {  // unconditional second pass
+                    CK(multi_dot(Vp, nv, w, N, nrhs, ws.as<double>(), sq2p, s));
+                    CK(gs_coef(sq2p, coef.as<double>(), hacc.as<double>(), nv * nrhs, false, s));
+                    CK(gs_update_norm(w, Vp, nv, coef.as<double>(), N, nrhs, nullptr, ws.as<double>(), hsb.as<double>(),
+                                      s));
                 }
-                CK(col_sumsq(w, N, nrhs, ws.as<double>(), sq.as<double>(), s));
                 CK(cudaMemcpyAsync(hh.data(), hacc.p, (size_t)(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost, s));
-                CK(cudaMemcpyAsync(hs.data(), sq.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(hs.data(), hsb.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 for (int i = 0; i <= j; ++i)
                     for (int q = 0; q < nrhs; ++q) Hq(q, i, j) = hh[(size_t)i * nrhs + q];

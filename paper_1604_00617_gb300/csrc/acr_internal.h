@@ -234,6 +234,20 @@ cudaError_t convert_f2d(const float* src, double* dst, long long n, cudaStream_t
 //   out[i * nrhs + q] = sum_r V_i[r, q] w[r, q]        (i < nvec), deterministic
 cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws,
                       double* out, cudaStream_t s);
+//   multi_dot, and out[nvec * nrhs + q] = sum_r w[r, q]^2
+cudaError_t multi_dot_self(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws,
+                           double* out, cudaStream_t s);
+//   w[r, q] += sum_i coef[i * nrhs + q] V_i[r, q] (nvec <= 64) and
+//   out[q] = |w_new[:, q]|^2, in one read of V.  need != NULL: only the columns
+//   with need[q] (the others are neither read nor written).
+cudaError_t gs_update_norm(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
+                           const int* need, double* ws, double* out, cudaStream_t s);
+//   The second Gram-Schmidt pass where the first cancelled more than
+//   1 - ratio2 of the squared norm (sq1[q] < ratio2 sq0[q]): there h2 = V^T w,
+//   w -= V h2 and hacc += h2; hs[q] = |w_final|^2 for every column.  N <= 4M.
+cudaError_t gs_reorth(double* w, const double* V, int nvec, const double* sq0, const double* sq1, double ratio2,
+                      double* h2, double* coef, double* hacc, int* need, double* hs, long long N, int nrhs,
+                      double* ws, cudaStream_t s);
 //   w[r, q] += sum_i coef[i * nrhs + q] V_i[r, q]
 cudaError_t multi_axpy(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
                        cudaStream_t s);

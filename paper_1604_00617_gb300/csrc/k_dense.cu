@@ -1552,9 +1552,11 @@ constexpr int DW = 16;
 constexpr int DOT_VB = 64;  // vectors per shared-memory batch
 __global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ V, int nvec,
                                                      const double* __restrict__ w, long long N, int nrhs,
-                                                     double* __restrict__ ws) {
+                                                     double* __restrict__ ws, int selfdot,
+                                                     const int* __restrict__ need) {
     __shared__ double red[DOT_VB * 8];
     const int q = blockIdx.y, chunks = gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (need && !need[q]) return;  // column q not asked for: nothing written
     const long long lo = (long long)blockIdx.x * DW * 256;
     const double* wq = w + (long long)q * N;
     double wr[DW], v[DW];
@@ -1563,6 +1565,8 @@ __global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ 
         const long long r = lo + tid + u * 256;
         wr[u] = r < N ? wq[r] : 0.0;
     }
+    // selfdot: one more product after the nvec vectors, w with itself
+    const int ntot = nvec + (selfdot ? 1 : 0);
     if (nvec > 0) {
         const double* vq = V + (long long)q * N;
 #pragma unroll
@@ -1570,9 +1574,12 @@ __global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ 
             const long long r = lo + tid + u * 256;
             v[u] = r < N ? vq[r] : 0.0;
         }
+    } else {
+#pragma unroll
+        for (int u = 0; u < DW; ++u) v[u] = wr[u];
     }
-    for (int i0 = 0; i0 < nvec; i0 += DOT_VB) {
-        const int i1 = min(nvec, i0 + DOT_VB);
+    for (int i0 = 0; i0 < ntot; i0 += DOT_VB) {
+        const int i1 = min(ntot, i0 + DOT_VB);
         for (int i = i0; i < i1; ++i) {
             double sum = 0.0;
 #pragma unroll
@@ -1584,6 +1591,9 @@ __global__ void __launch_bounds__(256) k_multi_dot_w(const double* __restrict__ 
                     const long long r = lo + tid + u * 256;
                     v[u] = r < N ? vq[r] : 0.0;
                 }
+            } else if (i + 1 == nvec) {
+#pragma unroll
+                for (int u = 0; u < DW; ++u) v[u] = wr[u];
             }
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (lane == 0) red[(i - i0) * 8 + warp] = sum;
@@ -1611,7 +1621,7 @@ cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, i
     // the workspace holds 1024 partials per product
     const long long cw = (N + (long long)DW * 256 - 1) / ((long long)DW * 256);
     if (cw <= 1024) {
-        k_multi_dot_w<<<dim3((int)cw, nrhs), 256, 0, s>>>(V, nvec, w, N, nrhs, ws);
+        k_multi_dot_w<<<dim3((int)cw, nrhs), 256, 0, s>>>(V, nvec, w, N, nrhs, ws, 0, nullptr);
         count_launches(1);
         k_sumsq_final<<<nvec * nrhs, 256, 0, s>>>(ws, (int)cw, out);
         count_launches(1);
@@ -1623,6 +1633,134 @@ cudaError_t multi_dot(const double* V, int nvec, const double* w, long long N, i
     k_sumsq_final<<<nvec * nrhs, 256, 0, s>>>(ws, chunks, out);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t multi_dot_self(const double* V, int nvec, const double* w, long long N, int nrhs, double* ws, double* out,
+                           cudaStream_t s) {
+    if (nrhs <= 0) return cudaSuccess;
+    const long long cw = (N + (long long)DW * 256 - 1) / ((long long)DW * 256);
+    if (cw <= 1024) {
+        k_multi_dot_w<<<dim3((int)cw, nrhs), 256, 0, s>>>(V, nvec, w, N, nrhs, ws, 1, nullptr);
+        count_launches(1);
+        k_sumsq_final<<<(nvec + 1) * nrhs, 256, 0, s>>>(ws, (int)cw, out);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    cudaError_t e = multi_dot(V, nvec, w, N, nrhs, ws, out, s);
+    if (e != cudaSuccess) return e;
+    return col_sumsq(w, N, nrhs, ws, out + (size_t)nvec * nrhs, s);
+}
+
+// One Gram-Schmidt correction with the squared norm of its result.  Grid
+// (G, nrhs); CTA (g, q) takes the 256-row tiles g, g + G, ... of column q,
+// thread t row t of each: w[r] += sum_i coef[i, q] V_i[r] in order i = 0, 1,
+// ..., accumulating w_new[r]^2 across its tiles; the CTA's sum (shuffles,
+// then warps in order) goes to ws[q * G + g].
+// need != NULL: column q is skipped unless need[q] (nothing written for it).
+__global__ void __launch_bounds__(256) k_gs_upd_norm(double* __restrict__ w, const double* __restrict__ V, int nvec,
+                                                     const double* __restrict__ coef, long long N, int nrhs,
+                                                     const int* __restrict__ need, double* __restrict__ ws) {
+    __shared__ double sc[64];
+    __shared__ double red[8];
+    const int q = blockIdx.y, G = gridDim.x, g = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (need && !need[q]) return;
+    for (int i = tid; i < nvec; i += 256) sc[i] = coef[(size_t)i * nrhs + q];
+    __syncthreads();
+    double* wq = w + (long long)q * N;
+    double acc = 0.0;
+    const long long ntile = (N + 255) / 256;
+    for (long long t = g; t < ntile; t += G) {
+        const long long r = t * 256 + tid;
+        const bool ok = r < N;
+        if (!ok) break;
+        double wn = wq[r];
+        const double* vp = V + (long long)q * N + r;
+        const long long vs = (long long)nrhs * N;
+#pragma unroll 4
+        for (int i = 0; i < nvec; ++i) wn = fma(sc[i], vp[i * vs], wn);
+        wq[r] = wn;
+        acc = fma(wn, wn, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double sm = 0.0;
+        for (int k = 0; k < 8; ++k) sm += red[k];
+        ws[(long long)q * G + g] = sm;
+    }
+}
+
+// CTAs per column of k_gs_upd_norm: a function of N only, so that a column's
+// summation order does not depend on how many columns share the call
+static int gs_groups(long long N) {
+    const long long ntile = (N + 255) / 256;
+    return (int)std::max(1LL, std::min(ntile, 304LL));
+}
+
+// out[q] = sum of column q's partials (k_sumsq_final), only where need[q]
+__global__ void k_final_need(const double* __restrict__ ws, int G, const int* __restrict__ need,
+                             double* __restrict__ out) {
+    __shared__ double red[32];
+    const int q = blockIdx.x;
+    if (need && !need[q]) return;
+    double sm = 0.0;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) sm += ws[(long long)q * G + i];
+    for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sm;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        sm = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        if (threadIdx.x == 0) out[q] = sm;
+    }
+}
+
+cudaError_t gs_update_norm(double* w, const double* V, int nvec, const double* coef, long long N, int nrhs,
+                           const int* need, double* ws, double* out, cudaStream_t s) {
+    if (nrhs <= 0) return cudaSuccess;
+    if (nvec > 64) return cudaErrorInvalidValue;
+    const int G = gs_groups(N);
+    k_gs_upd_norm<<<dim3(G, nrhs), 256, 0, s>>>(w, V, nvec, coef, N, nrhs, need, ws);
+    k_final_need<<<nrhs, 256, 0, s>>>(ws, G, need, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+// need[q] = |w'|^2 < ratio2 |w|^2;  hs[q] = |w'|^2
+__global__ void k_gs_need(const double* __restrict__ sq0, const double* __restrict__ sq1, double ratio2,
+                          int* __restrict__ need, double* __restrict__ hs, int nrhs) {
+    for (int q = threadIdx.x; q < nrhs; q += blockDim.x) {
+        need[q] = sq1[q] < ratio2 * sq0[q] ? 1 : 0;
+        hs[q] = sq1[q];
+    }
+}
+// where need[q]: coef = -h2, hacc += h2;  elsewhere coef = 0
+__global__ void k_gs_coef_need(const double* __restrict__ h2, const int* __restrict__ need,
+                               double* __restrict__ coef, double* __restrict__ hacc, int n, int nrhs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool nd = need[i % nrhs] != 0;
+        coef[i] = nd ? -h2[i] : 0.0;
+        if (nd) hacc[i] += h2[i];
+    }
+}
+
+cudaError_t gs_reorth(double* w, const double* V, int nvec, const double* sq0, const double* sq1, double ratio2,
+                      double* h2, double* coef, double* hacc, int* need, double* hs, long long N, int nrhs,
+                      double* ws, cudaStream_t s) {
+    if (nrhs <= 0) return cudaSuccess;
+    k_gs_need<<<1, 32, 0, s>>>(sq0, sq1, ratio2, need, hs, nrhs);
+    count_launches(1);
+    const long long cw = (N + (long long)DW * 256 - 1) / ((long long)DW * 256);
+    if (cw > 1024) return cudaErrorInvalidValue;
+    k_multi_dot_w<<<dim3((int)cw, nrhs), 256, 0, s>>>(V, nvec, w, N, nrhs, ws, 0, need);
+    count_launches(1);
+    k_sumsq_final<<<nvec * nrhs, 256, 0, s>>>(ws, (int)cw, h2);
+    count_launches(1);
+    k_gs_coef_need<<<(nvec * nrhs + 255) / 256, 256, 0, s>>>(h2, need, coef, hacc, nvec * nrhs, nrhs);
+    count_launches(1);
+    return gs_update_norm(w, V, nvec, coef, N, nrhs, need, ws, hs, s);
 }
 
 __global__ void k_multi_axpy(double* __restrict__ w, const double* __restrict__ V, int nvec,
