@@ -254,6 +254,30 @@ const char *acr_last_error(void);
 #define ACR_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int acr_block_inverse_noalloc(int blksz, int count, double *mats, int *info, void *stream);
 
+/* Batched low-rank truncation (Section 3: the recompression that follows
+ * every H-sum and H-product of the reduction in HODLR arithmetic, here on
+ * caller-supplied factors).  For each of `count` nodes, U_i and V_i (s x R,
+ * column-major, FP64, node i at offset i*s*R) define M_i = U_i V_i^T.  The
+ * kept rank r_i is the number of singular values of M_i above
+ * tol * sigma_1(M_i) (tol in [0, 1); at most min(s, R)).  Outputs, same
+ * layout: Vout_i holds r_i orthonormal columns spanning the leading right
+ * singular vectors, then zero columns; Uout_i = U_i V_i^T Vout_i, so that
+ * Uout_i Vout_i^T is the truncation of M_i; ranks[i] = r_i.
+ *
+ * Method: QR of U, Y = V R_U^T, QR of Y, one-sided Jacobi SVD of R_Y (the
+ * exact pass); with sketch = k > 0 (k < min(s, R)) the randomized first pass
+ * instead works on the range of U (V^T Omega) for a k-column Rademacher
+ * Omega, and a node whose rank comes within 6 of k is redone by the exact
+ * pass (*exact_redo, if not NULL, receives how many).  precision: ACR_FP64,
+ * or ACR_FP32TC_IR / ACR_FP32_IR for FP32 arithmetic (inputs and outputs
+ * stay FP64).  U, V, Uout, Vout, ranks may be host or device memory (of the
+ * current device); the caller owns them.  Synchronous.  Errors:
+ * ACR_ERR_INVALID_ARG (sizes, NULL, tol, memory of another GPU, panels above
+ * the kernel's shared memory), ACR_ERR_OOM, ACR_ERR_CUDA. */
+int acr_lowrank_truncate(int count, int s, int R, const double *U, const double *V, double tol,
+                         int precision, int sketch, double *Uout, double *Vout, int *ranks,
+                         int *exact_redo);
+
 #ifdef __cplusplus
 }
 #endif

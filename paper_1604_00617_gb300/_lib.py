@@ -48,7 +48,7 @@ _NAMES = {0: "ACR_OK", -1: "ACR_ERR_INVALID_ARG", -2: "ACR_ERR_OOM", -3: "ACR_ER
 # every symbol include/acr.h declares
 EXPORTED = ["acr_default_opts", "acr_factor", "acr_factor_ex", "acr_solve", "acr_solve_ex",
             "acr_free", "acr_stats", "acr_factor_bytes", "acr_solve_bytes", "acr_last_error",
-            "acr_block_inverse_noalloc"]
+            "acr_block_inverse_noalloc", "acr_lowrank_truncate"]
 
 # fixed scratch of acr_block_inverse_noalloc (ACR_NOALLOC_SCRATCH_BYTES)
 ACR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH):
     lib.acr_last_error.restype = ctypes.c_char_p
     lib.acr_block_inverse_noalloc.argtypes = [i, i, vp, vp, vp]
     lib.acr_block_inverse_noalloc.restype = i
+    lib.acr_lowrank_truncate.argtypes = [i, i, i, vp, vp, ctypes.c_double, i, i, vp, vp, vp, vp]
+    lib.acr_lowrank_truncate.restype = i
     return lib
 
 
@@ -259,3 +261,21 @@ def acr_block_inverse_noalloc(blksz: int, count: int, mats, info, stream=None) -
     iptr = ctypes.c_void_p(info.data_ptr())
     _check(_lib.acr_block_inverse_noalloc(int(blksz), int(count), _ptr(mats, blksz * blksz * count), iptr,
                                           ctypes.c_void_p(stream) if stream else None))
+
+
+def acr_lowrank_truncate(U, V, tol: float, precision: int = ACR_FP64, sketch: int = 0):
+    """``acr_lowrank_truncate`` on host arrays: U, V of shape (count, R, s)
+    (node i's s x R factor column-major, i.e. numpy's [i, col, row]).  Returns
+    (Uout, Vout, ranks, exact_redo) in the same layout."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    if U.ndim != 3 or U.shape != V.shape:
+        raise ValueError("U and V must have the same shape (count, R, s)")
+    count, R, s = U.shape
+    Uo = np.zeros_like(U)
+    Vo = np.zeros_like(V)
+    rk = np.zeros(count, dtype=np.int32)
+    redo = ctypes.c_int(0)
+    _check(_lib.acr_lowrank_truncate(count, s, R, _ptr(U), _ptr(V), float(tol), int(precision), int(sketch),
+                                     _ptr(Uo), _ptr(Vo), ctypes.c_void_p(rk.ctypes.data), ctypes.byref(redo)))
+    return Uo, Vo, rk, redo.value

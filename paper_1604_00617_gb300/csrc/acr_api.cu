@@ -2055,3 +2055,175 @@ int acr_stats(acr_handle h, acr_stats_t* s) {
 }
 
 }  // extern "C"
+
+namespace {
+template <class T>
+int lowrank_truncate_impl(int count, int s, int R, const double* dU, const double* dV, double tol, int sketch,
+                          double* dUo, double* dVo, int* dranks, std::vector<int>& hr, cudaStream_t st) {
+    using namespace acr;
+    const size_t nel = (size_t)count * s * R;
+    DevBuf bU, bV, bVo, bUo, bW, bR2, bP;
+    const T *U, *V;
+    T *Vo, *Uo;
+    if (sizeof(T) == 8) {
+        U = reinterpret_cast<const T*>(dU);
+        V = reinterpret_cast<const T*>(dV);
+        Vo = reinterpret_cast<T*>(dVo);
+        Uo = reinterpret_cast<T*>(dUo);
+    } else {
+        CK(bU.alloc(nel * sizeof(T), st));
+        CK(bV.alloc(nel * sizeof(T), st));
+        CK(bVo.alloc(nel * sizeof(T), st));
+        CK(bUo.alloc(nel * sizeof(T), st));
+        CK(convert_d2f(dU, bU.as<float>(), (long long)nel, st));
+        CK(convert_d2f(dV, bV.as<float>(), (long long)nel, st));
+        U = reinterpret_cast<const T*>(bU.p);
+        V = reinterpret_cast<const T*>(bV.p);
+        Vo = reinterpret_cast<T*>(bVo.p);
+        Uo = reinterpret_cast<T*>(bUo.p);
+    }
+    RPT<T> P;
+    memset(&P, 0, sizeof(P));
+    P.U.base = U;
+    P.U.gs = (long long)s * R;
+    P.U.ld = s;
+    P.V = P.U;
+    P.V.base = V;
+    P.Vout = P.U;
+    P.Vout.base = Vo;
+    P.s = s;
+    P.R = R;
+    P.wout = R;
+    P.ni = 1;
+    P.ng = count;
+    const int kcap = std::min(s, R);
+    if (hrecomp_smem_bytes(s, R, sizeof(T)) > 227 * 1024)
+        return fail(ACR_ERR_INVALID_ARG, "s = %d, R = %d: the panels exceed the truncation kernel's shared memory", s, R);
+    int ks = sketch;
+    if (ks > 0 && (ks >= std::min(s, R) || hrecomp_sketch_smem_bytes(s, R, ks, sizeof(T)) > 227 * 1024)) ks = 0;
+    CK(hrecomp_t<T>(P, dranks, tol, kcap, ks, st));
+    CK(cudaMemcpyAsync(hr.data(), dranks, count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<RProb<T>> redo;
+    std::vector<int> at;
+    for (int i = 0; i < count; ++i)
+        if (hr[i] < 0) {
+            RProb<T> q;
+            q.U = U + (size_t)i * s * R;
+            q.V = V + (size_t)i * s * R;
+            q.Vout = Vo + (size_t)i * s * R;
+            q.ldu = q.ldv = q.ldvo = s;
+            q.s = s;
+            q.R = R;
+            q.wout = R;
+            redo.push_back(q);
+            at.push_back(i);
+        }
+    if (!redo.empty()) {
+        CK(bP.alloc(redo.size() * sizeof(RProb<T>), st));
+        CK(bR2.alloc(redo.size() * sizeof(int), st));
+        CK(cudaMemcpyAsync(bP.p, redo.data(), redo.size() * sizeof(RProb<T>), cudaMemcpyHostToDevice, st));
+        CK(hrecomp<T>(bP.as<RProb<T>>(), (int)redo.size(), s, R, bR2.as<int>(), tol, kcap, st));
+        std::vector<int> r2(redo.size());
+        CK(cudaMemcpyAsync(r2.data(), bR2.p, r2.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t j = 0; j < at.size(); ++j) hr[at[j]] = -2 - r2[j];  // -2 - rank: resolved by the exact pass
+        std::vector<int> fixed(hr);
+        for (int& v : fixed) v = v <= -2 ? -2 - v : v;
+        CK(cudaMemcpyAsync(dranks, fixed.data(), count * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    CK(bW.alloc((size_t)count * R * R * sizeof(T), st));
+    CK(lowrank_apply<T>(U, V, Vo, bW.as<T>(), Uo, count, s, R, st));
+    if (sizeof(T) == 4) {
+        CK(convert_f2d(bVo.as<float>(), dVo, (long long)nel, st));
+        CK(convert_f2d(bUo.as<float>(), dUo, (long long)nel, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return ACR_OK;
+}
+}  // namespace
+
+extern "C" int acr_lowrank_truncate(int count, int s, int R, const double* U, const double* V, double tol,
+                                    int precision, int sketch, double* Uout, double* Vout, int* ranks,
+                                    int* exact_redo) {
+    if (count < 0 || s < 1 || R < 1) return fail(ACR_ERR_INVALID_ARG, "count >= 0, s >= 1 and R >= 1 required");
+    if (count == 0) {
+        if (exact_redo) *exact_redo = 0;
+        return ACR_OK;
+    }
+    if (!U || !V || !Uout || !Vout || !ranks) return fail(ACR_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol >= 0.0) || tol >= 1.0) return fail(ACR_ERR_INVALID_ARG, "tol must lie in [0, 1) (got %g)", tol);
+    if (precision != ACR_FP64 && precision != ACR_FP32TC_IR && precision != ACR_FP32_IR)
+        return fail(ACR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (sketch < 0) return fail(ACR_ERR_INVALID_ARG, "sketch must be >= 0 (got %d)", sketch);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ACR_ERR_CUDA, "no usable CUDA device");
+    }
+    const void* ptrs[5] = {U, V, Uout, Vout, ranks};
+    PtrKind pk[5];
+    for (int i = 0; i < 5; ++i) {
+        pk[i] = ptr_kind(ptrs[i], dev);
+        if (pk[i] == PTR_OTHER_DEVICE) return fail(ACR_ERR_INVALID_ARG, "argument %d is memory of another GPU", i + 1);
+    }
+    const size_t nel = (size_t)count * s * R;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ACR_ERR_CUDA, "stream creation failed");
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } sg{st};
+    int rc = ACR_OK;
+    std::vector<int> hr(count);
+    {
+        DevBuf b[5];
+        double* d[4];
+        int* dr = ranks;
+        for (int i = 0; i < 4; ++i) {
+            d[i] = const_cast<double*>(static_cast<const double*>(ptrs[i]));
+            if (pk[i] != PTR_DEVICE) {
+                if (b[i].alloc(nel * 8, st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ACR_ERR_OOM, "device allocation failed");
+                }
+                if (i < 2 && cudaMemcpyAsync(b[i].p, ptrs[i], nel * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ACR_ERR_CUDA, "copy failed");
+                }
+                d[i] = b[i].as<double>();
+            }
+        }
+        if (pk[4] != PTR_DEVICE) {
+            if (b[4].alloc((size_t)count * sizeof(int), st) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ACR_ERR_OOM, "device allocation failed");
+            }
+            dr = b[4].as<int>();
+        }
+        rc = precision == ACR_FP64
+                 ? lowrank_truncate_impl<double>(count, s, R, d[0], d[1], tol, sketch, d[2], d[3], dr, hr, st)
+                 : lowrank_truncate_impl<float>(count, s, R, d[0], d[1], tol, sketch, d[2], d[3], dr, hr, st);
+        if (rc == ACR_OK) {
+            bool ok = true;
+            if (pk[2] != PTR_DEVICE) ok &= cudaMemcpyAsync(Uout, d[2], nel * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            if (pk[3] != PTR_DEVICE) ok &= cudaMemcpyAsync(Vout, d[3], nel * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            if (pk[4] != PTR_DEVICE)
+                ok &= cudaMemcpyAsync(ranks, dr, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            ok &= cudaStreamSynchronize(st) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                rc = fail(ACR_ERR_CUDA, "copy back failed");
+            }
+        }
+    }
+    if (exact_redo) {
+        int c = 0;
+        for (int v : hr) c += v <= -2;
+        *exact_redo = c;
+    }
+    return rc;
+}

@@ -401,4 +401,8 @@ cudaError_t hcopy_t(const CPT<T>& P, cudaStream_t s);
 template <class T>
 cudaError_t hrecomp_t(const RPT<T>& P, int* ranks, double tol, int kcap, int ks, cudaStream_t st);
 size_t hrecomp_sketch_smem_bytes(int s, int R, int ks, int es);
+// Uo_i = U_i (V_i^T Vp_i) for count nodes of s x R (node stride s R); W holds
+// count x R x R
+template <class T>
+cudaError_t lowrank_apply(const T* U, const T* V, const T* Vp, T* W, T* Uo, int count, int s, int R, cudaStream_t st);
 }  // namespace acr

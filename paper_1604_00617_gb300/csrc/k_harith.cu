@@ -603,6 +603,48 @@ size_t hrecomp_smem_bytes(int s, int R, int es) {
     return es == 8 ? hrecomp_smem<double>(s, R) : hrecomp_smem<float>(s, R);
 }
 
+// U'_i = U_i (V_i^T V'_i) for count nodes of s x R (node stride s R):
+// W_i = V_i^T V'_i (R x R, in W), then U'_i = U_i W_i.  One thread per output
+// element, sums in index order.
+template <class T>
+__global__ void k_lr_w(const T* __restrict__ V, const T* __restrict__ Vp, T* __restrict__ W, int count, int s, int R) {
+    const long long n = (long long)count * R * R;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long node = e / ((long long)R * R);
+        const int ab = (int)(e % ((long long)R * R)), a = ab % R, b2 = ab / R;
+        const T* v = V + node * s * R + (long long)a * s;
+        const T* vp = Vp + node * s * R + (long long)b2 * s;
+        T acc = T(0);
+        for (int r = 0; r < s; ++r) acc = fma(v[r], vp[r], acc);
+        W[e] = acc;
+    }
+}
+template <class T>
+__global__ void k_lr_u(const T* __restrict__ U, const T* __restrict__ W, T* __restrict__ Uo, int count, int s, int R) {
+    const long long n = (long long)count * s * R;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long node = e / ((long long)s * R);
+        const int rb = (int)(e % ((long long)s * R)), r = rb % s, b2 = rb / s;
+        const T* u = U + node * s * R + r;
+        const T* w = W + node * R * R + (long long)b2 * R;
+        T acc = T(0);
+        for (int a = 0; a < R; ++a) acc = fma(u[(long long)a * s], w[a], acc);
+        Uo[e] = acc;
+    }
+}
+template <class T>
+cudaError_t lowrank_apply(const T* U, const T* V, const T* Vp, T* W, T* Uo, int count, int s, int R, cudaStream_t st) {
+    if (count <= 0 || s <= 0 || R <= 0) return cudaSuccess;
+    k_lr_w<T><<<1024, 256, 0, st>>>(V, Vp, W, count, s, R);
+    k_lr_u<T><<<1024, 256, 0, st>>>(U, W, Uo, count, s, R);
+    count_launches(2);
+    return cudaGetLastError();
+}
+template cudaError_t lowrank_apply<float>(const float*, const float*, const float*, float*, float*, int, int, int,
+                                          cudaStream_t);
+template cudaError_t lowrank_apply<double>(const double*, const double*, const double*, double*, double*, int, int,
+                                           int, cudaStream_t);
+
 size_t hrecomp_sketch_smem_bytes(int s, int R, int ks, int es) {
     return es == 8 ? hrecomp_sk_smem<double>(s, R, ks) : hrecomp_sk_smem<float>(s, R, ks);
 }

@@ -145,3 +145,15 @@ def test_noalloc_rejects_host_memory_without_launching(lib):
     assert (mats == np.eye(4).ravel()).all() and info[0] == 0
     with pytest.raises(TypeError):
         lib.acr_block_inverse_noalloc(4, 1, mats, info)
+
+
+def test_lowrank_truncate_rejects_bad_arguments_on_host(lib):
+    import numpy as np
+    U = np.zeros((2, 3, 4))
+    for kw, msg in ((dict(tol=-1.0), "tol"), (dict(tol=1.0), "tol"), (dict(tol=1e-3, precision=9), "precision"),
+                    (dict(tol=1e-3, sketch=-2), "sketch")):
+        with pytest.raises(lib.AcrError) as ei:
+            lib.acr_lowrank_truncate(U, U, **kw)
+        assert ei.value.code == lib.ACR_ERR_INVALID_ARG and msg in lib.acr_last_error()
+    with pytest.raises(ValueError):
+        lib.acr_lowrank_truncate(U, np.zeros((2, 3, 5)), 1e-3)
