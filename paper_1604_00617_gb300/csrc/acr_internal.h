@@ -260,6 +260,32 @@ cudaError_t col_scale(double* v, const double* w, const double* scale, long long
 
 }  // namespace acr
 
+#ifdef __CUDACC__
+namespace acr {
+// Tangent of a Jacobi rotation, zeta = (beta - alpha) / (2 gamma): the root
+// of t^2 + 2 zeta t - 1 = 0 of smaller magnitude.  For |zeta| > 1 the square
+// root is taken as |zeta| sqrt(1 + 1/zeta^2): zeta^2 overflows once |zeta|
+// passes ~1e19 in FP32 (a tiny column against a large one), and the t = 0
+// that follows would leave the pair as it is while still counting it as
+// rotated, so the sweeps would never end.
+// Whether a Jacobi pair (squared norms al, be, product ga) needs a rotation:
+// |ga| > eps |a| |b|, with the norms taken apart (al * be underflows for tiny
+// columns in FP32), and never for a pair with a zero norm: a column whose
+// squares underflow can still have a nonzero product with a large one, and
+// its zeta is infinite, so the rotation would be the identity forever.
+template <class T>
+__device__ __forceinline__ bool jacobi_needs(T al, T be, T ga, T eps) {
+    return al > T(0) && be > T(0) && ga != T(0) && fabs(ga) > eps * sqrt(al) * sqrt(be);
+}
+template <class T>
+__device__ __forceinline__ T jacobi_tan(T zeta) {
+    const T az = fabs(zeta);
+    const T root = az > T(1) ? az * sqrt(T(1) + (T(1) / az) * (T(1) / az)) : sqrt(T(1) + az * az);
+    return (zeta >= T(0) ? T(1) : T(-1)) / (az + root);
+}
+}  // namespace acr
+#endif
+
 // --- HODLR arithmetic of the low reduction levels (k_harith.cu) -------------
 // Batched products of different sizes: C[M x N] = beta * Cin + sum over the
 // problem's terms t0 .. t0 + nt - 1 of alpha * op(A) op(B), op(A) M x K and

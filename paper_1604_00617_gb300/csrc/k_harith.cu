@@ -330,10 +330,15 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
         const int k = r0;
         for (int e = tid; e < s * R; e += 256) Pn[e] = Pr.V[(size_t)(e % s) + (size_t)(e / s) * Pr.ldv];
         __syncthreads();
+        // (the row index starts at j in the loops below, so that the threads
+        // of a warp, which hold different j, read different banks)
         for (int e = tid; e < R * k; e += 256) {  // Wk = V^T Omega
             const int j = e % R, c = e / R;
             T acc = T(0);
-            for (int r = 0; r < s; ++r) acc = fma(Pn[r + (size_t)j * s], (T)rademacher(r, c), acc);
+            for (int t = 0; t < s; ++t) {
+                const int r = (t + j) % s;
+                acc = fma(Pn[r + (size_t)j * s], (T)rademacher(r, c), acc);
+            }
             Wk[e] = acc;
         }
         __syncthreads();
@@ -365,7 +370,10 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
         for (int e = tid; e < R * k; e += 256) {  // Wk = U^T Q
             const int j = e % R, c = e / R;
             T acc = T(0);
-            for (int r = 0; r < s; ++r) acc = fma(Pn[r + (size_t)j * s], Qp[r + (size_t)c * s], acc);
+            for (int t = 0; t < s; ++t) {
+                const int r = (t + j) % s;
+                acc = fma(Pn[r + (size_t)j * s], Qp[r + (size_t)c * s], acc);
+            }
             Wk[e] = acc;
         }
         __syncthreads();
@@ -423,7 +431,10 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
     }
     __syncthreads();
     // ---- one-sided Jacobi on the columns of R_Y (round-robin pairs) ----------
-    const T eps = sizeof(T) == 8 ? T(4e-15) : T(4e-7);
+    // a pair counts as orthogonal when |a.b| <= ke u |a| |b|: the rounding of
+    // a dot product of ke terms is about that size, so a tighter test would
+    // keep rotating columns at the noise level (FP32) without converging
+    const T eps = T(ke) * (sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-7));
     {
         T part = T(0);
         for (int e = tid; e < ke * ke; e += 256) part += RY[e] * RY[e];
@@ -440,11 +451,12 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
     const T negl = red[8] * (sizeof(T) == 8 ? T(1e-28) : T(1e-13));
     __syncthreads();
     // Squared column norms are kept in sv (recomputed each sweep, updated by
-    // every rotation: ||a'||^2 = ||a||^2 - t g, ||b'||^2 = ||b||^2 + t g).  A
-    // pair whose two columns are both below 1e-2 tol times the largest
-    // initial column norm (a lower bound of sigma_1) is left alone: whatever
-    // the rotations do, those columns stay far below the truncation level,
-    // so they cannot change the kept singular values or the rank.
+    // every rotation: ||a'||^2 = ||a||^2 - t g, ||b'||^2 = ||b||^2 + t g) for
+    // the skip test only: a pair whose two columns are both below 1e-2 tol
+    // times the largest initial column norm (a lower bound of sigma_1) is
+    // left alone: whatever the rotations do, those columns stay far below the
+    // truncation level, so they cannot change the kept singular values or
+    // the rank.
     T* cn = sv;
     for (int c = warp; c < ke; c += 8) {
         T n2 = T(0);
@@ -478,16 +490,25 @@ __device__ void hrecomp_body(const RProb<T>& Pr, int* __restrict__ rank_out, T t
                     int a, bc;
                     if (q == 0) { a = ke - 1; bc = rnd; }
                     else { a = (rnd + q) % (ke - 1); bc = (rnd - q + (ke - 1)) % (ke - 1); }
-                    const T al = cn[a], be = cn[bc];
-                    if (!(al + be > skip2)) continue;  // uniform over the warp
+                    if (!(cn[a] + cn[bc] > skip2)) continue;  // uniform over the warp
                     T* ca = RY + (size_t)a * ke;
                     T* cb = RY + (size_t)bc * ke;
-                    T ga = T(0);
-                    for (int r = lane; r < ke; r += 32) ga += ca[r] * cb[r];
+                    // the rotation from the pair's own norms (norms carried
+                    // over from earlier rotations drift at the noise level,
+                    // and a rotation from drifted norms need not orthogonalise)
+                    T ga = T(0), al = T(0), be = T(0);
+                    for (int r = lane; r < ke; r += 32) {
+                        const T x = ca[r], y = cb[r];
+                        ga = fma(x, y, ga);
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                    }
                     ga = hwarp_sum(ga);
-                    if (fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                    al = hwarp_sum(al);
+                    be = hwarp_sum(be);
+                    if (jacobi_needs(al, be, ga, eps)) {
                         const T zeta = (be - al) / (T(2) * ga);
-                        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        const T t = jacobi_tan(zeta);
                         const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
                         for (int r = lane; r < ke; r += 32) {
                             const T x = ca[r], y = cb[r];

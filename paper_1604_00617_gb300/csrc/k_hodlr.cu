@@ -455,9 +455,9 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
 #pragma unroll
                 for (int r = 0; r < 32; ++r) ga = fma(col[r], pc[r], ga);
                 const T al = is_a ? nrm : pn, be = is_a ? pn : nrm;
-                if (partner != lane && al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                if (partner != lane && al + be > negl && jacobi_needs(al, be, ga, eps)) {
                     const T zeta = (be - al) / (T(2) * ga);
-                    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    const T t = jacobi_tan(zeta);
                     const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
                     T n2 = T(0);
                     if (is_a) {
@@ -503,9 +503,9 @@ __global__ void __launch_bounds__(256) k_node_svd(const T* __restrict__ Yall, T*
                     al += x * x; be += y * y; ga += x * y;
                 }
                 al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+                if (al + be > negl && jacobi_needs(al, be, ga, eps)) {
                     const T zeta = (be - al) / (T(2) * ga);
-                    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    const T t = jacobi_tan(zeta);
                     const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
                     for (int r = lane; r < k; r += 32) {
                         const T x = ca[r], y = cb[r];
@@ -673,9 +673,9 @@ k_node_svd_w(const T* __restrict__ Yall, T* __restrict__ Uall, T* __restrict__ s
 #pragma unroll
             for (int r = 0; r < KK; ++r) ga = fma(cl[r], pc[r], ga);
             const T al = is_a ? nrm : pn, be = is_a ? pn : nrm;
-            if (partner != lane && al + be > negl && fabs(ga) > eps * sqrt(al * be) && ga != T(0)) {
+            if (partner != lane && al + be > negl && jacobi_needs(al, be, ga, eps)) {
                 const T zeta = (be - al) / (T(2) * ga);
-                const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                const T t = jacobi_tan(zeta);
                 const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
                 T n2 = T(0);
                 if (is_a) {
