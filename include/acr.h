@@ -111,7 +111,11 @@ typedef struct {
 /* Largest off-diagonal rank of a level's blocks for which the automatic
  * choice (h_levels = 0) continues in HODLR arithmetic.  A level also goes
  * dense when its HODLR inverses miss the identity on random vectors by more
- * than 1e4 times the truncation tolerance (see h_check in acr_stats_t).  The
+ * than 1e4 times the truncation tolerance (see h_check in acr_stats_t), and
+ * for the FP32 factor the automatic choice tries no further level once the
+ * misses' growth, extrapolated geometrically from the last two levels,
+ * passes that limit (there the miss grows by orders of magnitude per level
+ * once the reduced blocks turn ill-conditioned).  The
  * HODLR arithmetic truncates at max(tol / 10, a few units of the factor's
  * rounding), so that the truncations accumulated over the levels keep the
  * solve near tol. */

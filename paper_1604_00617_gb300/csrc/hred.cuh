@@ -1311,6 +1311,21 @@ int reduce(Red<T>& R, int n, const double* Dband, const T* a, const T* c, int hm
         int mr = 0;
         for (int l = 1; l <= L; ++l) mr = std::max({mr, D->maxrank(l), AC->maxrank(l)});
         if ((hmax > 0 && t >= hmax) || mr > hrank) break;
+        // automatic choice in FP32: the next level is not tried when the
+        // checks' growth, extrapolated geometrically (c_t^2 / c_{t-1}, with
+        // c_{t-1} taken at least 1e-3 of the limit), passes the limit.  In
+        // FP32 the check grows by orders of magnitude per level once the
+        // reduced blocks turn ill-conditioned (Helmholtz 1024^2: 1.5e-7,
+        // 3e-7, 6.5e-3, then 12 against a limit of 9.5e-3), and such a level
+        // would fail its check only after its whole H-inverse had been built.
+        // FP64 checks move up and down by orders of magnitude between levels
+        // (and every level done in HODLR arithmetic there is more accurate
+        // than a dense level compressed afterwards), so FP64 tries them all.
+        if (sizeof(T) == 4 && hmax <= 0 && res.check.size() >= 2) {
+            const double c1 = res.check[res.check.size() - 1];
+            const double c0 = std::max(res.check[res.check.size() - 2], 1e-3 * chk_max);
+            if (c1 * (c1 / c0) > chk_max) break;
+        }
     }
     R.drop_tmp();
     res.th = t;
