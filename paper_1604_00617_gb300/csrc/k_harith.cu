@@ -1021,9 +1021,138 @@ __global__ void __launch_bounds__(256) k_vgemm_t(const __grid_constant__ VPT<T> 
     }
 }
 
+// Products with at most 8 output columns, one warp per (problem, row tile),
+// 8 warps per CTA, no shared memory and no barrier.
+//   KL (M <= 8): lane l computes the outputs l and l + 32 of the M x N
+//     block (column-major order): the rank x rank products V^T U of the
+//     HODLR arithmetic, a handful of outputs over a long inner dimension.
+//   !KL: lane l owns rows r0 + l and r0 + l + 32 of a 64-row tile.
+// Every output is summed exactly as the tile kernel sums it (terms in order,
+// k ascending, acc = fma(alpha op(A)[m, k], op(B)[k, n], acc), then
+// + beta Cin), so the two give bitwise the same results.  A lane split of the
+// inner dimension, more accurate per product, was measured to change the
+// rounding of the HODLR inverses enough to raise the FGMRES iterations of the
+// 1024^2 Helmholtz solve from 21 to 25; the order is kept.
+template <class T, int NN, bool KL>
+__global__ void __launch_bounds__(256) k_vgemm_w(const __grid_constant__ VPT<T> P, int tpm, long long nwork) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long w = (long long)blockIdx.x * 8 + warp;
+    if (w >= nwork) return;
+    const long long p = w / tpm;
+    const int tile = (int)(w - p * tpm);
+    const int g = (int)(p / P.ni), i = (int)(p - (long long)g * P.ni);
+    T* C = const_cast<T*>(haddr(P.C, g, i));
+    if (!C) return;
+    const T* Cin = haddr(P.Cin, g, i);
+    const int M = P.M, N = P.N;
+    if (KL) {
+        const int o0 = lane, o1 = lane + 32;
+        const bool ok0 = o0 < M * N, ok1 = o1 < M * N;
+        const int m0 = ok0 ? o0 % M : 0, n0 = ok0 ? o0 / M : 0;
+        const int m1 = ok1 ? o1 % M : 0, n1 = ok1 ? o1 / M : 0;
+        if (!ok0) return;  // no output for this lane (lanes are not synchronised below)
+        T acc0 = T(0), acc1 = T(0);
+        for (int t = 0; t < P.nt; ++t) {
+            const VTT<T>& Tm = P.t[t];
+            const T* A = haddr(Tm.A, g, i);
+            const T* B = haddr(Tm.B, g, i);
+            if (!A || !B) continue;
+            const bool ta = Tm.flags & 1, tb = Tm.flags & 2;
+            const long long lda = Tm.A.ld, ldb = Tm.B.ld;
+            // element (m, k) of op(A) at A + m * sam + k * sak, (k, n) of op(B) at B + k * sbk + n * sbn
+            const long long sam = ta ? lda : 1, sak = ta ? 1 : lda, sbk = tb ? ldb : 1, sbn = tb ? 1 : ldb;
+            const T* a0 = A + m0 * sam;
+            const T* b0 = B + n0 * sbn;
+            const T* a1 = A + m1 * sam;
+            const T* b1 = B + n1 * sbn;
+            const T al = Tm.alpha;
+            if (ok1) {
+#pragma unroll 4
+                for (int k = 0; k < Tm.K; ++k) {
+                    acc0 = fma(al * a0[k * sak], b0[k * sbk], acc0);
+                    acc1 = fma(al * a1[k * sak], b1[k * sbk], acc1);
+                }
+            } else {
+#pragma unroll 8
+                for (int k = 0; k < Tm.K; ++k) acc0 = fma(al * a0[k * sak], b0[k * sbk], acc0);
+            }
+        }
+        {
+            T v = acc0;
+            if (Cin) v += P.beta * Cin[(size_t)m0 + (size_t)n0 * P.Cin.ld];
+            C[(size_t)m0 + (size_t)n0 * P.C.ld] = v;
+        }
+        if (ok1) {
+            T v = acc1;
+            if (Cin) v += P.beta * Cin[(size_t)m1 + (size_t)n1 * P.Cin.ld];
+            C[(size_t)m1 + (size_t)n1 * P.C.ld] = v;
+        }
+    } else {
+        const int r0 = tile * 64 + lane, r1 = r0 + 32;
+        const bool ok0 = r0 < M, ok1 = r1 < M;
+        T acc0[NN], acc1[NN];
+#pragma unroll
+        for (int n = 0; n < NN; ++n) acc0[n] = acc1[n] = T(0);
+        for (int t = 0; t < P.nt; ++t) {
+            const VTT<T>& Tm = P.t[t];
+            const T* A = haddr(Tm.A, g, i);
+            const T* B = haddr(Tm.B, g, i);
+            if (!A || !B) continue;
+            const bool ta = Tm.flags & 1, tb = Tm.flags & 2;
+            const int lda = Tm.A.ld, ldb = Tm.B.ld;
+            const T al = Tm.alpha;
+#pragma unroll 4
+            for (int k = 0; k < Tm.K; ++k) {
+                const T a0 = ok0 ? al * (ta ? A[(size_t)k + (size_t)r0 * lda] : A[(size_t)r0 + (size_t)k * lda]) : T(0);
+                const T a1 = ok1 ? al * (ta ? A[(size_t)k + (size_t)r1 * lda] : A[(size_t)r1 + (size_t)k * lda]) : T(0);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) {
+                    const T bv = n < N ? (tb ? B[(size_t)n + (size_t)k * ldb] : B[(size_t)k + (size_t)n * ldb]) : T(0);
+                    acc0[n] = fma(a0, bv, acc0[n]);
+                    acc1[n] = fma(a1, bv, acc1[n]);
+                }
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            if (n >= N) continue;
+            if (ok0) {
+                T v = acc0[n];
+                if (Cin) v += P.beta * Cin[(size_t)r0 + (size_t)n * P.Cin.ld];
+                C[(size_t)r0 + (size_t)n * P.C.ld] = v;
+            }
+            if (ok1) {
+                T v = acc1[n];
+                if (Cin) v += P.beta * Cin[(size_t)r1 + (size_t)n * P.Cin.ld];
+                C[(size_t)r1 + (size_t)n * P.C.ld] = v;
+            }
+        }
+    }
+}
+
+template <class T, int NN>
+cudaError_t vgemm_w_launch(const VPT<T>& P, bool kl, cudaStream_t s) {
+    const int tpm = kl ? 1 : (P.M + 63) / 64;
+    const long long nwork = (long long)P.ng * P.ni * tpm;
+    const long long nb = (nwork + 7) / 8;
+    if (nb >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (kl) k_vgemm_w<T, NN, true><<<(unsigned)nb, 256, 0, s>>>(P, tpm, nwork);
+    else k_vgemm_w<T, NN, false><<<(unsigned)nb, 256, 0, s>>>(P, tpm, nwork);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t vgemm_t(const VPT<T>& P, cudaStream_t s) {
     if (P.M <= 0 || P.N <= 0 || P.ni <= 0 || P.ng <= 0) return cudaSuccess;
+    if (P.N <= 8) {
+        // at most 8 output columns: one warp per problem and 64-row tile
+        const bool kl = P.M <= 8;
+        if (P.N <= 1) return vgemm_w_launch<T, 1>(P, kl, s);
+        if (P.N <= 2) return vgemm_w_launch<T, 2>(P, kl, s);
+        if (P.N <= 4) return vgemm_w_launch<T, 4>(P, kl, s);
+        return vgemm_w_launch<T, 8>(P, kl, s);
+    }
     const bool narrow = P.N <= VN_BN;
     const int tpm = (P.M + VG_BM - 1) / VG_BM, tpn = (P.N + (narrow ? VN_BN : VG_BN) - 1) / (narrow ? VN_BN : VG_BN);
     const long long n = (long long)P.ng * P.ni * tpm * tpn;
