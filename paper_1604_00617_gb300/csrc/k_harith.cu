@@ -15,17 +15,24 @@
 // pointer offset, which turns every step of the arithmetic into batches of
 // small dense products over row ranges of these panels.
 //
-// Kernels:
-//   k_vgemm    batched products of different sizes: C = beta Cin + sum_t alpha_t op(A_t) op(B_t)
-//   k_hrecomp  truncation of one low-rank sum U V^T per node: Householder QR of U,
+// Kernels (list form: one descriptor per problem; _t form: one address
+// template per launch, problems found from the block and node index):
+//   k_vgemm(_t)  batched products of different sizes: C = beta Cin + sum_t alpha_t op(A_t) op(B_t)
+//   k_vgemm_w    the same with at most 8 output columns, one warp per problem
+//   k_hrecomp(_t) truncation of one low-rank sum U V^T per node: Householder QR of U,
 //              Y = V R_U^T, Householder QR of Y, one-sided Jacobi SVD of R_Y,
 //              V' = Q_Y W (the leading right singular vectors of U V^T, rank by
-//              sigma_k > tol sigma_1); U' = U (V^T V') follows by k_vgemm
-//   k_hcopy    scaled (optionally row-scaled) copies of panels between blocks
+//              sigma_k > tol sigma_1); U' = U (V^T V') follows by k_vgemm.  A
+//              randomized mode works on the range of U (V^T Omega) instead
+//   k_hcopy(_t)  scaled (optionally row-scaled) copies of panels between blocks
+//   k_tri_leaf_inv, k_gj_reg  FP64 inverses of the leaves (tridiagonal level-0
+//              leaves in O(leaf^2); pivoted Gauss-Jordan in registers) and of
+//              the capacitance matrices
 //   k_hkmat    the (2K x 2K) capacitance matrices [[I, T_b], [T_a, I]] of the
 //              Woodbury steps of the inverse, in FP64
 //   k_hband    the level-0 blocks of a 5-point operator in this format
 //   k_hpack    nodes of finished blocks into the solve's pool (U, then V^T)
+//   k_lr_w, k_lr_u  U' = U (V^T V') for the stand-alone truncation entry
 #include <cuda_runtime.h>
 
 #include <algorithm>

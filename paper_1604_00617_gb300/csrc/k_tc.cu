@@ -3,7 +3,10 @@
 // The Schur complement products of Eq. "fund" (D_j^-1 A_j, D_j^-1 C_j and
 // D_i - A_i XC_{i-1} - C_i XA_{i+1}, ...) are dense b x b contractions.  This
 // kernel runs them with tcgen05.mma (kind::tf32, FP32 accumulation in TMEM)
-// at FP32 accuracy by the three-term split  x ~= hi + lo,  hi = x rounded to
+// at FP32 accuracy by the error-corrected TF32 product (Ootomo and Yokota,
+// "Recovering single precision accuracy from Tensor Cores while surpassing
+// the FP32 theoretical peak performance", IJHPCA 2022): the three-term
+// split  x ~= hi + lo,  hi = x rounded to
 // the nearest TF32 value,  lo = (x - hi) rounded to the nearest TF32 value:
 //     A B  ~=  Ahi Bhi + Ahi Blo + Alo Bhi       (the Alo Blo term is ~2^-22;
 // launches that feed cancelling updates, the inversion's, add it as a fourth).
