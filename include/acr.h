@@ -205,6 +205,8 @@ typedef struct {
                                             max_j ||D_j (D_j^-1 x) - x|| / ||x|| on random x */
     long long h_nodes;                   /* node truncations in HODLR arithmetic */
     long long h_sketch_redo;             /* of which the sketch left to the exact pass */
+    long long sweep_passes;              /* preconditioner applications (forward +
+                                            back-substitution sweeps) in sweep_ms */
 } acr_stats_t;
 
 /* Copy the handle's statistics into *s. */

@@ -84,7 +84,8 @@ class acr_stats_t(ctypes.Structure):
                 ("launches_solve", ctypes.c_longlong), ("compress_ms", ctypes.c_double),
                 ("h_levels", ctypes.c_int), ("h_ms", ctypes.c_double), ("h_flops", ctypes.c_double),
                 ("h_host_ms", ctypes.c_double), ("h_check", ctypes.c_double * 32),
-                ("h_nodes", ctypes.c_longlong), ("h_sketch_redo", ctypes.c_longlong)]
+                ("h_nodes", ctypes.c_longlong), ("h_sketch_redo", ctypes.c_longlong),
+                ("sweep_passes", ctypes.c_longlong)]
 
 
 def load(path: str = LIB_PATH):

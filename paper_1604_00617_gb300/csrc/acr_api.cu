@@ -1816,6 +1816,7 @@ int refine(acr_ctx* h, const double* f, double* x, int nrhs, bool x0_given, std:
         h->st.sweep_ms += P.sp.elapsed_ms();
         h->st.sweep_bytes += P.sp.bytes * P.sp.passes();
         h->st.sweep_launches += P.sp.launches;
+        h->st.sweep_passes += P.sp.passes();
     }
     if (!conv)
         return fail(ACR_ERR_NOT_CONVERGED, "refinement took %d preconditioner solves without ||r||/||b|| <= %g (worst %g)",
@@ -1845,6 +1846,7 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
         h->st.sweep_ms = 0.0;
         h->st.sweep_bytes = 0.0;
         h->st.sweep_launches = 0;
+        h->st.sweep_passes = 0;
     }
     const long long lc0 = launch_count();
     CK(cudaEventRecord(e0, s));
@@ -1866,6 +1868,7 @@ int solve_impl(acr_ctx* h, double* B, int nrhs, double* resid_out, int* iters_ou
                 h->st.sweep_ms += sp.elapsed_ms();
                 h->st.sweep_bytes += sp.bytes;
                 h->st.sweep_launches += sp.launches;
+                h->st.sweep_passes += 1;
             }
             status = refine<double>(h, f, x.as<double>(), nrhs, true, rel, iters);
         } else {

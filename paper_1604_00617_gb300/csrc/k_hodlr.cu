@@ -852,6 +852,13 @@ __device__ __forceinline__ T xval(const HSweepProb<T>& P, int term, int r, int q
     return P.x[term][o];
 }
 
+// Programmatic dependent launch: the sweep's kernels are launched so that a
+// kernel's CTAs may start while its predecessor drains; every kernel reads
+// only static data (descriptors, node tables, the factor pool) before this
+// wait, and reads or writes the level vectors only after it, when the
+// predecessor's writes are complete and visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Pass A: t = V^T x for one low-rank node per CTA.  x[cols] is staged in
 // shared memory (coalesced); lane = g * rp + i handles rank index i (rp: rank
 // rounded up to a power of two, <= 32) for rows j = g, g + G, ... of its
@@ -877,6 +884,7 @@ k_hnode_t(const HSweepProb<T>* __restrict__ probs, const HTask* __restrict__ tas
     while (rp < rlo) rp <<= 1;
     const int G = 32 / rp, g = lane / rp, i0 = lane % rp;
     const int slice = (s + 7) / 8, j0 = warp * slice, j1 = min(s, j0 + slice);
+    pdl_wait();
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         __syncthreads();
@@ -961,6 +969,7 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
         s_rk[i] = tk.toff >= 0 ? hn.rank : 0;
         s_off[i] = hn.off;
     }
+    pdl_wait();
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         __syncthreads();
@@ -1069,6 +1078,7 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
     const int row = R0 + rg * V;
     const int warp = tid >> 5, lane = tid & 31;
     const int nz = gridDim.z, z = blockIdx.z;
+    pdl_wait();
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         // this thread's final outputs (i = tid, tid + 256 < RT * NR): cin early
@@ -1183,7 +1193,7 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
                 const T* __restrict__ mp = s_ptr[sg] + rg * V;
                 const int ld = s_ld[sg];
                 int j = cb + ((g - cb) % KG + KG) % KG;
-#pragma unroll 4
+#pragma unroll 8
                 for (; j < ce; j += KG) {
                     const VT mv = *reinterpret_cast<const VT*>(mp + (size_t)(j - cs) * ld);
                     const T* mvp = reinterpret_cast<const T*>(&mv);
@@ -1244,6 +1254,7 @@ k_hrows_w(const HSweepProb<T>* __restrict__ probs, const HNode* __restrict__ nod
     const int RG = RT / V, KG = 32 / RG;
     const int rg = lane % RG, g = lane / RG;
     const int row = R0 + rg * V;
+    pdl_wait();
     for (int q0 = 0; q0 < nrhs; q0 += NR) {
         const int nq = min(NR, nrhs - q0);
         T acc[V][NR];
@@ -1379,6 +1390,7 @@ k_hrows_w(const HSweepProb<T>* __restrict__ probs, const HNode* __restrict__ nod
 template <class T>
 __global__ void k_hrows_reduce(const HSweepProb<T>* __restrict__ probs, int nprob, int b, int nrhs, int nsplit,
                                const T* __restrict__ part) {
+    pdl_wait();
     const long long total = (long long)nprob * b * nrhs;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -1392,6 +1404,24 @@ __global__ void k_hrows_reduce(const HSweepProb<T>* __restrict__ probs, int npro
         if (P.cin) o += P.cin[row + (size_t)q * P.ldc];
         P.out[row + (size_t)q * P.ldo] = o;
     }
+}
+
+// Launch with programmatic stream serialization (the kernel may start while
+// the previous kernel on the stream drains; it waits in pdl_wait()).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sm, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
 template <class T>
@@ -1438,32 +1468,36 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     const bool per_term = terms != nullptr && rkmax <= 64 && L <= 6 && smt(8) <= 160 * 1024;
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
     {                                                                                                            \
+        cudaError_t le = cudaSuccess;                                                                            \
         if (per_term) {                                                                                          \
             if (nterms >= 152) {                                                                                 \
                 ensure_smem((const void*)k_hnodes<T, NRV, 256>, smT);                                          \
-                k_hnodes<T, NRV, 256><<<nterms, 256, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH,    \
-                                                               nrhs, std::max(rkmax, 1), tbuf);                  \
+                le = launch_pdl(k_hnodes<T, NRV, 256>, dim3(nterms), dim3(256), smT, s, probs_all, terms, tasks, \
+                                nodes, pool, b, L, CH, nrhs, std::max(rkmax, 1), tbuf);                          \
                 count_launches(1);                                                                               \
             } else if (nterms > 0) { /* less than a wave: four times the warps per term */                      \
                 ensure_smem((const void*)k_hnodes<T, NRV, 1024>, smT);                                         \
-                k_hnodes<T, NRV, 1024><<<nterms, 1024, smT, s>>>(probs_all, terms, tasks, nodes, pool, b, L, CH,  \
-                                                                 nrhs, std::max(rkmax, 1), tbuf);                \
+                le = launch_pdl(k_hnodes<T, NRV, 1024>, dim3(nterms), dim3(1024), smT, s, probs_all, terms,      \
+                                tasks, nodes, pool, b, L, CH, nrhs, std::max(rkmax, 1), tbuf);                   \
                 count_launches(1);                                                                               \
             }                                                                                                    \
         } else if (na > 0) {                                                                                     \
             ensure_smem((const void*)k_hnode_t<T, NRV>, smA);                                                  \
-            k_hnode_t<T, NRV><<<na, 256, smA, s>>>(probs_all, tasks, alist + a_off, nodes, pool, b, nrhs, tbuf);  \
+            le = launch_pdl(k_hnode_t<T, NRV>, dim3(na), dim3(256), smA, s, probs_all, tasks, alist + a_off,     \
+                            nodes, pool, b, nrhs, tbuf);                                                         \
             count_launches(1);                                                                                   \
         }                                                                                                        \
+        if (le != cudaSuccess) return le;                                                                        \
         if (by_warp) {                                                                                           \
             ensure_smem((const void*)k_hrows_w<T, NRV, V>, smW);                                               \
-            k_hrows_w<T, NRV, V><<<dim3((b / RT + 7) / 8, nprob), 256, smW, s>>>(                              \
-                probs_all + prob_off, nodes, tasks, tbuf, pool, b, leaf, L, nrhs, RT, wslice);                   \
+            le = launch_pdl(k_hrows_w<T, NRV, V>, dim3((b / RT + 7) / 8, nprob), dim3(256), smW, s,            \
+                            probs_all + prob_off, nodes, tasks, tbuf, pool, b, leaf, L, nrhs, RT, wslice);       \
         } else {                                                                                                 \
             ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                  \
-            k_hrows<T, NRV, V><<<gb, 256, sm, s>>>(probs_all + prob_off, blks, nodes, tasks, tbuf, pool, b, leaf,\
-                                                   L, nrhs, RT, part);                                           \
+            le = launch_pdl(k_hrows<T, NRV, V>, gb, dim3(256), sm, s, probs_all + prob_off, blks, nodes, tasks,  \
+                            tbuf, pool, b, leaf, L, nrhs, RT, part);                                             \
         }                                                                                                        \
+        if (le != cudaSuccess) return le;                                                                        \
         count_launches(1);                                                                                       \
     }
     if (NR == 1) ACR_HS_LAUNCH(1)
@@ -1473,7 +1507,10 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     if (part) {
         const long long tot = (long long)nprob * b * nrhs;
         const int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
-        k_hrows_reduce<T><<<blocks, 256, 0, s>>>(probs_all + prob_off, nprob, b, nrhs, nsplit, part);
+        const cudaError_t le =
+            launch_pdl(k_hrows_reduce<T>, dim3(blocks), dim3(256), 0, s, probs_all + prob_off, nprob, b, nrhs, nsplit,
+                       (const T*)part);
+        if (le != cudaSuccess) return le;
         count_launches(1);
         cudaFreeAsync(part, s);
     }
