@@ -58,6 +58,10 @@ def parse():
     p.add_argument("--no-dense", action="store_true", help="skip the dense-block (tol 0) comparison")
     p.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving mix (0: skip)")
     p.add_argument("--serving-rate", type=float, default=200.0, help="offered rate of the serving mix, req/s")
+    p.add_argument("--tol-study", default="",
+                   help="comma-separated HODLR tolerances: instead of the benchmark line, one JSON line per "
+                        "tolerance with factor time, ranks, FGMRES iterations and time to 1e-8 (the factor as a "
+                        "preconditioner of tunable accuracy)")
     return p.parse_args()
 
 
@@ -334,6 +338,9 @@ def run_ours(args):
         o.stream = ctypes.c_void_p(stream.cuda_stream)
         return o
 
+    if args.tol_study:
+        tol_study(args, acr, P, prec, opts, da, dD3, dc, dF, dB, stream)
+        return
     o = opts(prec)
     stats = []
 
@@ -536,6 +543,49 @@ def _smi_id(dev):
         return u if u.startswith("GPU-") else "GPU-" + u
     except Exception:
         return None
+
+
+def tol_study(args, acr, P, prec, opts, da, dD3, dc, dF, dB, stream):
+    """Section 5's "ACR as a preconditioner": factor at a loose HODLR
+    tolerance (fewer ranks, a cheaper factor and cheaper sweeps) and let FGMRES
+    make up the accuracy.  One JSON line per tolerance: factor seconds, stored
+    bytes, ranks, iterations and the time to a 1e-8 residual (median of
+    --steps factor + solve steps after --warmup)."""
+    import torch
+    for tol in (float(x) for x in args.tol_study.split(",")):
+        rows = []
+        for k in range(args.warmup + args.steps):
+            o = opts(prec)
+            o.ir_max_iter = 300  # a loose factor may need more FGMRES steps than the benchmark allows
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = acr.acr_factor_ex(P.nblk, P.b, da, dD3, dc, tol, o)
+            t1 = time.perf_counter()
+            try:
+                dB.copy_(dF)
+                res, it = acr.acr_solve_ex(h, dB, args.nrhs)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                s = acr.acr_stats(h)
+                conv = True
+            except acr.AcrError as e:
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                s, res, it, conv = acr.acr_stats(h), None, -1, False
+            finally:
+                acr.acr_free(h)
+            if k >= args.warmup:
+                rows.append((t1 - t0, t2 - t1, s, it, conv, res))
+        fs = statistics.median(r[0] for r in rows)
+        ss = statistics.median(r[1] for r in rows)
+        s, it, conv, res = rows[-1][2], rows[-1][3], rows[-1][4], rows[-1][5]
+        print(json.dumps({"study": "tol", "tol": tol, "precision": prec, "n": args.n, "nrhs": args.nrhs,
+                          "factor_s": fs, "solve_s": ss, "time_to_1e8_s": fs + ss, "converged": conv,
+                          "iters": it, "resid_max": float(max(res)) if res is not None else None,
+                          "solves_per_s": args.nrhs / (fs + ss) if conv else 0.0,
+                          "h_levels": s["h_levels"], "factor_bytes": s["factor_bytes"],
+                          "rank_max": s["rank_max"], "rank_mean": [round(x, 2) for x in s["rank_mean"]],
+                          "sweep_ms_per_application": s["sweep_ms"] / max(1, s["sweep_passes"])}), flush=True)
 
 
 def main():
