@@ -81,6 +81,7 @@ class Record:
     resid: float = 0.0
     iters: int = 0
     batch: int = 1
+    sys_rid: int = -1     # a solve's system
 
 
 def peak_bytes(req: SystemRequest, precision: int) -> int:
@@ -314,7 +315,7 @@ class Server:
                         self.records[r.rid] = Record(r.rid, "factor", t0 + r.arrival, r.nblk)
                         self.sys_queue.append(r)
                     else:
-                        self.records[r.rid] = Record(r.rid, "solve", t0 + r.arrival)
+                        self.records[r.rid] = Record(r.rid, "solve", t0 + r.arrival, sys_rid=r.sys_rid)
                         if self.remaining.get(r.sys_rid, 0) < 0:
                             self.records[r.rid].ok = False
                             self.records[r.rid].done = time.perf_counter()
@@ -342,6 +343,19 @@ def summarize(records, wall: float) -> dict:
         lat = np.array([(r.done - r.arrival) * 1e3 for r in records.values() if r.kind == kind and r.ok])
         if lat.size:
             out[kind] = {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+    # solves whose system was already factored when they arrived (resident):
+    # their latency is the solve's own wait and run, while the others also
+    # wait for their system's factorization
+    def fdone(r):
+        f = records.get(r.sys_rid)
+        return f.done if f is not None and f.kind == "factor" and f.ok else float("inf")
+    for name, sel in (("solve_resident", lambda r: fdone(r) <= r.arrival),
+                      ("solve_before_factor_done", lambda r: fdone(r) > r.arrival)):
+        lat = np.array([(r.done - r.arrival) * 1e3 for r in records.values()
+                        if r.kind == "solve" and r.ok and sel(r)])
+        if lat.size:
+            out[name] = {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
     nsolve = sum(1 for r in records.values() if r.kind == "solve" and r.ok)
     out["solves_per_s"] = nsolve / wall if wall > 0 else 0.0

@@ -226,6 +226,19 @@ def test_summary():
     assert s["failed"] == 0 and s["solves_per_s"] > 0
 
 
+def test_summary_splits_solves_by_residency():
+    """Solves that arrive after their system's factorization has finished are
+    reported apart from those that also wait for it."""
+    lib = FakeLib(tf=0.05, ts=0.002)
+    # two solves arrive during the 50 ms factorization, two well after it
+    ev = _stream([(0.0, 8, [0.001, 0.002, 0.2, 0.21])])
+    srv = serving.Server(1 << 40, slots=2, lib=lib, new_stream=FakeStream)
+    recs, wall = srv.run(ev)
+    s = serving.summarize(recs, wall)
+    assert s["solve_before_factor_done"]["count"] == 2 and s["solve_resident"]["count"] == 2
+    assert s["solve_resident"]["p99_ms"] < 40 < s["solve_before_factor_done"]["p50_ms"]
+
+
 def test_request_stream_seeded():
     e1 = serving.make_requests(30, rate=100.0, seed=3, sizes=(8, 16), probs=(0.5, 0.5), max_solves=5)
     e2 = serving.make_requests(30, rate=100.0, seed=3, sizes=(8, 16), probs=(0.5, 0.5), max_solves=5)
