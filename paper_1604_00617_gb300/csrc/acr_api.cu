@@ -1137,6 +1137,7 @@ struct SweepPlan {
     DevBuf hterms;                   // compressed terms with low-rank nodes: (problem << 1) | term
     std::vector<size_t> t_start;     // first entry (in hterms) of every problem
     int rkmax = 0;                   // largest rank of a low-rank node
+    std::vector<int> prk;            // largest low-rank node rank of every problem
     std::vector<int> pwmax;          // widest row tile of every problem
     bool hodlr = false;
     std::vector<size_t> fw_g_off, fw_g_cnt, fw_f_off, fw_f_cnt, bk_off, bk_cnt;
@@ -1389,6 +1390,16 @@ int build_sweep(acr_ctx* h, T* F0, int nrhs, SweepPlan<T>& sp) {
         for (size_t pi = 0; pi < hp.size(); ++pi)
             for (int t = 0; t < 2; ++t)
                 if (hp[pi].blk[t] >= 0 && !hp[pi].dg[t]) sp.pwmax[pi] = std::max(sp.pwmax[pi], bw[hp[pi].blk[t]]);
+        // largest low-rank node of every problem: pass A sizes its partial
+        // sums by the launch's largest rank, not the plan's
+        std::vector<int> brk(h->hblks_host.size(), 0);
+        for (size_t g = 0; g < brk.size(); ++g)
+            for (int nu = 0; nu < h->npb; ++nu)
+                brk[g] = std::max(brk[g], h->hnodes_host[(size_t)h->hblks_host[g].node_base + nu].rank);
+        sp.prk.assign(hp.size(), 0);
+        for (size_t pi = 0; pi < hp.size(); ++pi)
+            for (int t = 0; t < 2; ++t)
+                if (hp[pi].blk[t] >= 0 && !hp[pi].dg[t]) sp.prk[pi] = std::max(sp.prk[pi], brk[hp[pi].blk[t]]);
         CK(sp.hterms.alloc(std::max<size_t>(1, terms.size()) * sizeof(int), s));
         if (!terms.empty())
             CK(cudaMemcpyAsync(sp.hterms.p, terms.data(), terms.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1449,10 +1460,13 @@ int issue_sweep(acr_ctx* h, SweepPlan<T>& sp) {
         auto seg = [&](size_t off, size_t cnt) -> cudaError_t {
             const size_t a0 = sp.a_start[off], a1 = sp.a_start[off + cnt];
             const size_t t0 = sp.t_start[off], t1 = sp.t_start[off + cnt];
-            int wmax = 0;
-            for (size_t pi = off; pi < off + cnt; ++pi) wmax = std::max(wmax, sp.pwmax[pi]);
+            int wmax = 0, rk = 0;
+            for (size_t pi = off; pi < off + cnt; ++pi) {
+                wmax = std::max(wmax, sp.pwmax[pi]);
+                rk = std::max(rk, sp.prk[pi]);
+            }
             return hsweep<T>(hq, (int)off, (int)cnt, tk, al, (int)a0, (int)(a1 - a0), tl + t0, (int)(t1 - t0),
-                             sp.rkmax, wmax, tb, hb, hn, pool, b, h->leaf, h->hL, nrhs, s);
+                             rk, wmax, tb, hb, hn, pool, b, h->leaf, h->hL, nrhs, s);
         };
         for (int t = 0; t <= T_; ++t) {
             CK(seg(sp.fw_g_off[t], sp.fw_g_cnt[t]));
