@@ -36,6 +36,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <cstdint>
 
 #include "acr_internal.h"
@@ -1150,15 +1154,131 @@ cudaError_t vgemm_w_launch(const VPT<T>& P, bool kl, cudaStream_t s) {
 }
 
 template <class T>
+cudaError_t vgemm_tile_launch(const VPT<T>& P, cudaStream_t s) {
+    const bool narrow = P.N <= VN_BN;
+    const int tpm = (P.M + VG_BM - 1) / VG_BM, tpn = (P.N + (narrow ? VN_BN : VG_BN) - 1) / (narrow ? VN_BN : VG_BN);
+    const long long n = (long long)P.ng * P.ni * tpm * tpn;
+    if (n >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (narrow) k_vgemm_t<T, true><<<(unsigned)n, 256, 0, s>>>(P, tpm, tpn);
+    else k_vgemm_t<T, false><<<(unsigned)n, 256, 0, s>>>(P, tpm, tpn);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Products with at most 8 output columns have three kernels that sum every
+// output in the same order (bitwise the same results): 0 the warp kernel
+// with lanes over outputs (M <= 8), 1 the warp kernel with lanes over rows,
+// 2 the tile kernel.
+template <class T>
+cudaError_t vgemm_small_launch(const VPT<T>& P, int cand, cudaStream_t s) {
+    if (cand == 2) return vgemm_tile_launch<T>(P, s);
+    const bool kl = cand == 0;
+    if (P.N <= 1) return vgemm_w_launch<T, 1>(P, kl, s);
+    if (P.N <= 2) return vgemm_w_launch<T, 2>(P, kl, s);
+    if (P.N <= 4) return vgemm_w_launch<T, 4>(P, kl, s);
+    return vgemm_w_launch<T, 8>(P, kl, s);
+}
+
+// Online tile autotuner for those products: per shape (element size, M, N,
+// the terms' inner dimensions, the number of problems) each candidate runs
+// on one of the shape's first launches between CUDA events, and once every
+// candidate's time is in, the fastest serves the shape from then on.  Since
+// the candidates give the same bits, the choice changes timing only.  No
+// candidate is timed inside a stream capture (the default runs there).
+struct VgKey {
+    int es, M, N, nt;
+    long long nprob;
+    int K[VT_MAXT];
+    bool operator<(const VgKey& o) const {
+        if (es != o.es) return es < o.es;
+        if (M != o.M) return M < o.M;
+        if (N != o.N) return N < o.N;
+        if (nt != o.nt) return nt < o.nt;
+        if (nprob != o.nprob) return nprob < o.nprob;
+        for (int i = 0; i < nt; ++i)
+            if (K[i] != o.K[i]) return K[i] < o.K[i];
+        return false;
+    }
+};
+struct VgTune {
+    int ncand = 0, next = 0, best = -1;
+    int cand[3] = {0, 0, 0};
+    cudaEvent_t ev[3][2] = {};
+    bool recorded[3] = {false, false, false};  // both events of candidate c are on a stream
+    bool timed[3] = {false, false, false};
+    float ms[3] = {0.f, 0.f, 0.f};
+};
+static std::mutex g_vg_mu;
+static std::map<VgKey, VgTune> g_vg;
+static std::atomic<long long> g_vg_tuned{0};  // shapes whose choice is made
+
+template <class T>
 cudaError_t vgemm_t(const VPT<T>& P, cudaStream_t s) {
     if (P.M <= 0 || P.N <= 0 || P.ni <= 0 || P.ng <= 0) return cudaSuccess;
     if (P.N <= 8) {
-        // at most 8 output columns: one warp per problem and 64-row tile
-        const bool kl = P.M <= 8;
-        if (P.N <= 1) return vgemm_w_launch<T, 1>(P, kl, s);
-        if (P.N <= 2) return vgemm_w_launch<T, 2>(P, kl, s);
-        if (P.N <= 4) return vgemm_w_launch<T, 4>(P, kl, s);
-        return vgemm_w_launch<T, 8>(P, kl, s);
+        VgKey key;
+        memset(&key, 0, sizeof(key));
+        key.es = (int)sizeof(T); key.M = P.M; key.N = P.N; key.nt = P.nt; key.nprob = (long long)P.ng * P.ni;
+        for (int i = 0; i < P.nt && i < VT_MAXT; ++i) key.K[i] = P.t[i].K;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) {
+            cudaGetLastError();
+            cst = cudaStreamCaptureStatusActive;
+        }
+        int cand = P.M <= 8 ? 0 : 1;  // the default
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_vg_mu);
+            VgTune& st = g_vg[key];
+            if (st.ncand == 0) {
+                if (P.M <= 8) st.cand[st.ncand++] = 0;
+                st.cand[st.ncand++] = 1;
+                st.cand[st.ncand++] = 2;
+            }
+            if (st.best < 0) {
+                bool all = true;
+                for (int c = 0; c < st.ncand; ++c) {
+                    if (!st.timed[c] && st.recorded[c] && cudaEventQuery(st.ev[c][1]) == cudaSuccess) {
+                        if (cudaEventElapsedTime(&st.ms[c], st.ev[c][0], st.ev[c][1]) != cudaSuccess)
+                            st.ms[c] = 3.0e38f;  // no usable time: never the fastest
+                        st.timed[c] = true;
+                    }
+                    all = all && st.timed[c];
+                }
+                cudaGetLastError();  // a pending event query is not an error
+                if (all) {
+                    int b = 0;
+                    for (int c = 1; c < st.ncand; ++c)
+                        if (st.ms[c] < st.ms[b]) b = c;
+                    st.best = b;
+                    g_vg_tuned.fetch_add(1);
+                }
+            }
+            if (st.best >= 0) {
+                cand = st.cand[st.best];
+            } else if (cst == cudaStreamCaptureStatusNone && st.next < st.ncand) {
+                const int c = st.next++;
+                if (cudaEventCreate(&st.ev[c][0]) == cudaSuccess && cudaEventCreate(&st.ev[c][1]) == cudaSuccess) {
+                    cand = st.cand[c];
+                    e0 = st.ev[c][0];
+                    e1 = st.ev[c][1];
+                } else {
+                    cudaGetLastError();
+                    st.ncand = c;  // time no further candidate
+                    st.best = c > 0 ? 0 : -1;
+                }
+            }
+        }
+        if (e0) cudaEventRecord(e0, s);
+        const cudaError_t e = vgemm_small_launch<T>(P, cand, s);
+        if (e1) {
+            cudaEventRecord(e1, s);
+            std::lock_guard<std::mutex> lk(g_vg_mu);
+            VgTune& st = g_vg[key];
+            for (int c = 0; c < st.ncand; ++c)
+                if (st.ev[c][1] == e1) st.recorded[c] = true;
+        }
+        return e;
     }
     const bool narrow = P.N <= VN_BN;
     const int tpm = (P.M + VG_BM - 1) / VG_BM, tpn = (P.N + (narrow ? VN_BN : VG_BN) - 1) / (narrow ? VN_BN : VG_BN);
