@@ -767,9 +767,11 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
         const int KOi = (b - K0) < KO ? (b - K0) : KO;
         for (int k0 = K0; k0 < K0 + KOi; k0 += KB) {
             const int kbi = (K0 + KOi - k0) < KB ? (K0 + KOi - k0) : KB;
-            if (kbi == KB && b <= 1024) {  // panel rows in registers, one per thread
+            if (kbi == KB && b <= 1024) {  // panel rows in registers
                 if (b <= 512) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
-                else k_gj_panel_reg<T, 1024, 1, KB><<<count, 1024, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+                // blocks above 512 rows: 512 threads with two rows each (fewer warps
+                // per barrier than one row per thread; the same pivots and bits)
+                else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
             } else {
                 kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
             }
