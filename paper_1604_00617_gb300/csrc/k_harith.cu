@@ -1386,8 +1386,10 @@ template cudaError_t hrecomp_t<double>(const RPT<double>&, int*, double, int, in
 // =============================================================================
 namespace acr {
 
+// (4 CTAs per SM: the matrices are latency-bound, one pivot step several
+// barriers, so more of them in flight keep the FP64 pipes busier)
 template <class T>
-__global__ void __launch_bounds__(256) k_gj_reg(T* __restrict__ mats, int b, int* __restrict__ info) {
+__global__ void __launch_bounds__(256, 4) k_gj_reg(T* __restrict__ mats, int b, int* __restrict__ info) {
     constexpr int B = 64, G = 16;
     __shared__ T rowk[B], colk[B], rowp[B];
     __shared__ T wv[8];
