@@ -1043,6 +1043,83 @@ k_hnodes(const HSweepProb<T>* __restrict__ probs, const int* __restrict__ terms,
     }
 }
 
+// Pass A for launches with few compressed terms: each term's items (CH rows
+// of one node's V, as in k_hnodes) are spread over gridDim.y CTAs, one warp
+// per item, the warp staging the CH rows of x its item reads.  Every item's
+// partial t (rank x nrhs) is computed exactly as k_hnodes computes it and
+// goes to gpart[(((2 p + term) * nitems + it) * rkmax + ii) * nrhs + q]
+// (p: the problem's index in the launch); pass B adds a node's items in item
+// order when it stages t, as k_hnodes's node sums do, so the results are the
+// same bits.
+template <class T, int NR>
+__global__ void __launch_bounds__(256)
+k_hnodes_sp(const HSweepProb<T>* __restrict__ probs, int prob_off, const int* __restrict__ terms,
+            const HTask* __restrict__ tasks, const HNode* __restrict__ nodes, const T* __restrict__ pool, int b, int L,
+            int CH, int nrhs, int rkmax, T* __restrict__ gpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* xw = reinterpret_cast<T*>(smem_raw) + (size_t)warp * CH * NR;  // this warp's CH x NR
+    const int e = terms[blockIdx.x];
+    const int p = e >> 1, term = e & 1, ep = 2 * (p - prob_off) + term;
+    const HSweepProb<T>& P = probs[p];
+    const int tb = P.tbase[term];
+    const int per_level = b / CH, nitems = L * per_level;
+    const int ipc = (nitems + gridDim.y - 1) / gridDim.y;
+    const int it0 = blockIdx.y * ipc, it1 = min(nitems, it0 + ipc);
+    pdl_wait();
+    for (int it = it0 + warp; it < it1; it += 8) {
+        const int l = 1 + it / per_level, u = it % per_level;
+        const int sz = b >> l, cpn = sz / CH;
+        const int ni = u / cpn, cc = u % cpn;
+        const int nu = (1 << l) - 2 + ni;
+        const HTask tk = tasks[tb + nu];
+        if (tk.toff < 0) continue;
+        const HNode hn = nodes[tk.node];
+        const int rk = hn.rank;
+        if (rk <= 0) continue;
+        const T* Vt = pool + hn.off + (size_t)sz * rk;
+        const int c0 = (ni ^ 1) * sz;
+        const int rlo = rk < 32 ? rk : 32;
+        int rp = 1;
+        while (rp < rlo) rp <<= 1;
+        const int G = 32 / rp, g = lane / rp, i0 = lane % rp;
+        const int j0 = cc * CH, j1 = j0 + CH;
+        T* gp = gpart + ((size_t)ep * nitems + it) * rkmax * nrhs;
+        for (int q0 = 0; q0 < nrhs; q0 += NR) {
+            const int nq = min(NR, nrhs - q0);
+            __syncwarp();
+            for (int i = lane; i < CH * NR; i += 32) {
+                const int jr = i % CH, q = i / CH;
+                xw[(size_t)jr * NR + q] = q < nq ? xval(P, term, c0 + j0 + jr, q0 + q) : T(0);
+            }
+            __syncwarp();
+            for (int ib = 0; ib < rk; ib += 32) {
+                const int ii = ib + i0;
+                const bool live = i0 < rp && ii < rk;
+                T acc[NR];
+#pragma unroll
+                for (int q = 0; q < NR; ++q) acc[q] = T(0);
+                if (live) {
+#pragma unroll 8
+                    for (int j = j0 + g; j < j1; j += G) {
+                        const T v = Vt[ii + (size_t)j * rk];
+                        const T* xr = xw + (size_t)(j - j0) * NR;
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] = fma(v, xr[q], acc[q]);
+                    }
+                }
+                for (int o = rp; o < 32; o <<= 1)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (g == 0 && live)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q)
+                        if (q < nq) gp[(size_t)ii * nrhs + q0 + q] = acc[q];
+            }
+        }
+    }
+}
+
 // 16-byte vectors of T for the row streams of pass B
 template <class T> struct HVec;
 template <> struct HVec<float> { using type = float4; static constexpr int V = 4; };
@@ -1064,7 +1141,7 @@ template <class T, int NR, int V>
 __global__ void __launch_bounds__(256)
 k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, const HNode* __restrict__ nodes,
         const HTask* __restrict__ tasks, const T* __restrict__ tbuf, const T* __restrict__ pool, int b, int leaf,
-        int L, int nrhs, int RT, T* __restrict__ part) {
+        int L, int nrhs, int RT, T* __restrict__ part, const T* __restrict__ gpart, int gCH, int grk) {
     using VT = typename HVec<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);  // [W][NR], W <= b; reused for the group sums
@@ -1174,8 +1251,22 @@ k_hrows(const HSweepProb<T>* __restrict__ probs, const HBlk* __restrict__ blks, 
                         while (s_cs[sg + 1] <= j) ++sg;
                         const int c = j - s_cs[sg];
                         if (q < nq) {
-                            if (s_kind[sg] == 1) xv[u] = tbuf[s_src[sg] + c + (size_t)(q0 + q) * s_rk[sg]];
-                            else xv[u] = xval(P, t, (int)s_src[sg] + c, q0 + q);
+                            if (s_kind[sg] == 1) {
+                                if (gpart) {
+                                    // t of the tile's node at level sg: its items' partials, in item order
+                                    const int sz = b >> sg, nj = R0 / sz, per_level = b / gCH, cpn = sz / gCH;
+                                    const int nitems = L * per_level, it0 = (sg - 1) * per_level + nj * cpn;
+                                    const T* gp = gpart + (((size_t)(2 * blockIdx.y + t) * nitems + it0) * grk + c) *
+                                                              nrhs + q0 + q;
+                                    T v = T(0);
+                                    for (int cc = 0; cc < cpn; ++cc) v += gp[(size_t)cc * grk * nrhs];
+                                    xv[u] = v;
+                                } else {
+                                    xv[u] = tbuf[s_src[sg] + c + (size_t)(q0 + q) * s_rk[sg]];
+                                }
+                            } else {
+                                xv[u] = xval(P, t, (int)s_src[sg] + c, q0 + q);
+                            }
                         }
                     }
                 }
@@ -1466,10 +1557,26 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     // decided at the widest chunk, so that every column count takes the same
     // kernel (and summation order)
     const bool per_term = terms != nullptr && rkmax <= 64 && L <= 6 && smt(8) <= 160 * 1024;
+    // few terms and the CTA-per-tile pass B: pass A's items spread over 8 CTAs
+    // per term, their partials added by pass B (same bits as k_hnodes)
+    const bool split_a = per_term && !by_warp && nterms > 0 && nterms < 152;
+    const int nitems_a = L * (b / CH);
+    T* gpart = nullptr;
+    if (split_a && cudaMallocAsync(&gpart, sizeof(T) * (size_t)nprob * 2 * nitems_a * std::max(rkmax, 1) * nrhs, s) !=
+                       cudaSuccess) {
+        cudaGetLastError();
+        if (part) cudaFreeAsync(part, s);
+        return cudaErrorMemoryAllocation;
+    }
 #define ACR_HS_LAUNCH(NRV)                                                                                       \
     {                                                                                                            \
         cudaError_t le = cudaSuccess;                                                                            \
-        if (per_term) {                                                                                          \
+        if (split_a) {                                                                                           \
+            le = launch_pdl(k_hnodes_sp<T, NRV>, dim3(nterms, (nitems_a + 7) / 8), dim3(256),                    \
+                            (size_t)8 * CH * NRV * sizeof(T), s, probs_all, prob_off, terms, tasks, nodes, pool, b, \
+                            L, CH, nrhs, std::max(rkmax, 1), gpart);                                             \
+            count_launches(1);                                                                                   \
+        } else if (per_term) {                                                                                   \
             if (nterms >= 152) {                                                                                 \
                 ensure_smem((const void*)k_hnodes<T, NRV, 256>, smT);                                          \
                 le = launch_pdl(k_hnodes<T, NRV, 256>, dim3(nterms), dim3(256), smT, s, probs_all, terms, tasks, \
@@ -1495,7 +1602,7 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
         } else {                                                                                                 \
             ensure_smem((const void*)k_hrows<T, NRV, V>, sm);                                                  \
             le = launch_pdl(k_hrows<T, NRV, V>, gb, dim3(256), sm, s, probs_all + prob_off, blks, nodes, tasks,  \
-                            tbuf, pool, b, leaf, L, nrhs, RT, part);                                             \
+                            tbuf, pool, b, leaf, L, nrhs, RT, part, (const T*)gpart, CH, std::max(rkmax, 1));    \
         }                                                                                                        \
         if (le != cudaSuccess) return le;                                                                        \
         count_launches(1);                                                                                       \
@@ -1504,6 +1611,7 @@ cudaError_t hsweep(const HSweepProb<T>* probs_all, int prob_off, int nprob, cons
     else if (NR == 4) ACR_HS_LAUNCH(4)
     else ACR_HS_LAUNCH(8)
 #undef ACR_HS_LAUNCH
+    if (gpart) cudaFreeAsync(gpart, s);
     if (part) {
         const long long tot = (long long)nprob * b * nrhs;
         const int blocks = (int)std::min<long long>((tot + 255) / 256, 152 * 8);
