@@ -294,6 +294,69 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+def rooflines(last, prec, peaks, clocks, gemm_tflops, b):
+    """The roofline entries of the bench line from the last step's stats:
+    the dense-level product kernel's (flops against the tensor or ALU peak)
+    and the compressed sweep's (algorithmic bytes per application against
+    the measured HBM copy rate).  Returns (the entry of the class with the
+    larger share of the step, the other entry's key, the other entry)."""
+    kernel = "gemm_tc" if prec == "fp32tc" else ("gemm_simt_f32" if prec == "fp32" else "gemm_simt_f64")
+    sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    pipe = None
+    if prec == "fp32tc":
+        # the contraction's own dtype is TF32: its peak is the measured bf16
+        # rate x the nominal tf32:bf16 ratio 1/2.  Each FP32-accurate product
+        # issues three TF32 MMAs (hi*hi + hi*lo + lo*hi), so the tensor pipe
+        # is busy 3x the algorithmic fraction; that figure is reported apart.
+        if peaks:
+            peak, src = (peaks["bf16_tflops_sustained"] / 2.0,
+                         "of measured: bf16 sustained x 1/2 (tf32 nominal ratio)")
+        else:
+            peak, src = 1700.0 / 2.0, "of fallback: 1.7 PFLOP/s bf16 sustained x 1/2 (tf32)"
+        pipe = {"frac": 3.0 * gemm_tflops / peak,
+                "note": "tensor-pipe busy fraction: 3 TF32 MMAs per algorithmic product (three-term split); "
+                        "the split's extra MMAs are not algorithmic work"}
+        bound = "tensor"
+    elif prec == "fp32":
+        peak, src = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"
+        bound = "alu"
+    else:
+        peak, src = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 2 FP64 FMA/clk x 2 x max SM clock"
+        bound = "alu"
+    tr = traffic_record(kernel) if kernel == "gemm_tc" else None
+    fpl = last["gemm_flops"] / max(1, last["gemm_launches"])
+    roof = {"kernel": kernel, "bound": bound, "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": gemm_tflops / peak, "peak_source": src,
+            "traffic": scaled_traffic(tr, fpl, b),
+            "traffic_source": (tr["capture"] + "; scaled by output elements to the average launch") if tr else None,
+            "algorithmic_per_launch": last["gemm_flops"] / max(1, last["gemm_launches"]),
+            "launch_ms": last["gemm_ms"] / max(1, last["gemm_launches"])}
+    if pipe:
+        roof["tensor_pipe_3xtf32"] = pipe
+    # the compressed sweeps (one application = forward + back-substitution
+    # over every level: pass A k_hnodes, pass B k_hrows*), HBM-bound: the
+    # algorithmic bytes of one application (every stored factor word read
+    # once, every input panel read and output panel written once) over the
+    # average application time, CUDA events around each application
+    sw_apps = max(1, int(last.get("sweep_passes", 0)))
+    hbm = (peaks or {}).get("hbm_gbs")
+    hbm_peak, hbm_src = (hbm, "of measured: STREAM-style copy") if hbm else (6800.0, "of fallback: 6.8 TB/s")
+    sweep_gbs = last["sweep_bytes"] / max(last["sweep_ms"], 1e-9) / 1e6
+    roof_sweep = {"kernel": "compressed sweep (k_hnodes + k_hrows_w / k_hrows + k_hrows_reduce per level)",
+                  "bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": sweep_gbs / hbm_peak, "peak_source": hbm_src,
+                  "traffic": None,
+                  "traffic_source": "null: the pass is some 77 launches of four kernels, not one kernel",
+                  "algorithmic_per_application_bytes": last["sweep_bytes"] / sw_apps,
+                  "application_ms": last["sweep_ms"] / sw_apps, "applications": sw_apps}
+    # the roofline line is the kernel class with the larger share of the step
+    if last["sweep_ms"] > last["gemm_ms"]:
+        roof_main, roof_other_key, roof_other = roof_sweep, "roofline_products", roof
+    else:
+        roof_main, roof_other_key, roof_other = roof, "roofline_sweep", roof_sweep
+    return roof_main, roof_other_key, roof_other
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -381,62 +444,9 @@ def run_ours(args):
     value = replica_value(nrhs * args.steps, ws, elapsed)
 
     last = stats[-1]
-    kernel = "gemm_tc" if prec == "fp32tc" else ("gemm_simt_f32" if prec == "fp32" else "gemm_simt_f64")
     peaks = measured_peaks()
     gemm_tflops = statistics.median(s["gemm_flops"] / (s["gemm_ms"] * 1e-3) / 1e12 for s in stats)
-    sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
-    pipe = None
-    if prec == "fp32tc":
-        # the contraction's own dtype is TF32: its peak is the measured bf16
-        # rate x the nominal tf32:bf16 ratio 1/2.  Each FP32-accurate product
-        # issues three TF32 MMAs (hi*hi + hi*lo + lo*hi), so the tensor pipe
-        # is busy 3x the algorithmic fraction; that figure is reported apart.
-        if peaks:
-            peak, src = (peaks["bf16_tflops_sustained"] / 2.0,
-                         "of measured: bf16 sustained x 1/2 (tf32 nominal ratio)")
-        else:
-            peak, src = 1700.0 / 2.0, "of fallback: 1.7 PFLOP/s bf16 sustained x 1/2 (tf32)"
-        pipe = {"frac": 3.0 * gemm_tflops / peak,
-                "note": "tensor-pipe busy fraction: 3 TF32 MMAs per algorithmic product (three-term split); "
-                        "the split's extra MMAs are not algorithmic work"}
-        bound = "tensor"
-    elif prec == "fp32":
-        peak, src = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"
-        bound = "alu"
-    else:
-        peak, src = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "derived: 152 SM x 2 FP64 FMA/clk x 2 x max SM clock"
-        bound = "alu"
-    tr = traffic_record(kernel) if kernel == "gemm_tc" else None
-    fpl = last["gemm_flops"] / max(1, last["gemm_launches"])
-    roof = {"kernel": kernel, "bound": bound, "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
-            "frac": gemm_tflops / peak, "peak_source": src,
-            "traffic": scaled_traffic(tr, fpl, P.b),
-            "traffic_source": (tr["capture"] + "; scaled by output elements to the average launch") if tr else None,
-            "algorithmic_per_launch": last["gemm_flops"] / max(1, last["gemm_launches"]),
-            "launch_ms": last["gemm_ms"] / max(1, last["gemm_launches"])}
-    if pipe:
-        roof["tensor_pipe_3xtf32"] = pipe
-    # the compressed sweeps (one application = forward + back-substitution
-    # over every level: pass A k_hnodes, pass B k_hrows*), HBM-bound: the
-    # algorithmic bytes of one application (every stored factor word read
-    # once, every input panel read and output panel written once) over the
-    # average application time, CUDA events around each application
-    sw_apps = max(1, int(last.get("sweep_passes", 0)))
-    hbm = (peaks or {}).get("hbm_gbs")
-    hbm_peak, hbm_src = (hbm, "of measured: STREAM-style copy") if hbm else (6800.0, "of fallback: 6.8 TB/s")
-    sweep_gbs = last["sweep_bytes"] / max(last["sweep_ms"], 1e-9) / 1e6
-    roof_sweep = {"kernel": "compressed sweep (k_hnodes + k_hrows_w / k_hrows + k_hrows_reduce per level)",
-                  "bound": "hbm", "achieved": sweep_gbs, "peak": hbm_peak, "unit": "GB/s",
-                  "frac": sweep_gbs / hbm_peak, "peak_source": hbm_src,
-                  "traffic": None,
-                  "traffic_source": "null: the pass is some 77 launches of four kernels, not one kernel",
-                  "algorithmic_per_application_bytes": last["sweep_bytes"] / sw_apps,
-                  "application_ms": last["sweep_ms"] / sw_apps, "applications": sw_apps}
-    # the roofline line is the kernel class with the larger share of the step
-    if last["sweep_ms"] > last["gemm_ms"]:
-        roof_main, roof_other_key, roof_other = roof_sweep, "roofline_gemm_tc", roof
-    else:
-        roof_main, roof_other_key, roof_other = roof, "roofline_sweep", roof_sweep
+    roof_main, roof_other_key, roof_other = rooflines(last, prec, peaks, clocks, gemm_tflops, P.b)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,

@@ -67,3 +67,29 @@ def test_peak_bytes_bounds_resident_bytes():
         assert pb >= acr.acr_factor_bytes(n, n, 0.0, o)
         assert pb > prev
         prev = pb
+
+
+def _stats(sweep_ms, gemm_ms):
+    return {"gemm_flops": 2.0 * 1024 ** 3 * 100, "gemm_launches": 10, "gemm_ms": gemm_ms,
+            "sweep_bytes": 2.0e9 * 21, "sweep_ms": sweep_ms, "sweep_passes": 21}
+
+
+def test_roofline_reports_the_larger_class():
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops_sustained": 1700.0}
+    clocks = {"sm_max_mhz": 2070.0}
+    main, key, other = bench.rooflines(_stats(47.0, 9.3), "fp32tc", peaks, clocks, 170.0, 1024)
+    assert main["bound"] == "hbm" and key == "roofline_products" and other["bound"] == "tensor"
+    # 2 GB per application in 47 / 21 ms
+    assert main["achieved"] == pytest.approx(2.0e9 * 21 / 47e-3 / 1e9)
+    assert main["frac"] == pytest.approx(main["achieved"] / 6800.0)
+    assert main["applications"] == 21 and main["application_ms"] == pytest.approx(47.0 / 21)
+    assert other["peak"] == pytest.approx(850.0) and other["frac"] == pytest.approx(170.0 / 850.0)
+    assert other["tensor_pipe_3xtf32"]["frac"] == pytest.approx(3 * 170.0 / 850.0)
+    main2, key2, _ = bench.rooflines(_stats(5.0, 9.3), "fp32tc", peaks, clocks, 170.0, 1024)
+    assert main2["bound"] == "tensor" and key2 == "roofline_sweep"
+
+
+def test_roofline_fallback_peaks():
+    main, _, other = bench.rooflines(_stats(47.0, 9.3), "fp32tc", None, {}, 170.0, 1024)
+    assert main["peak"] == 6800.0 and "fallback" in main["peak_source"]
+    assert "fallback" in other["peak_source"]
