@@ -739,7 +739,15 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
     constexpr int KB = sizeof(T) == 8 ? 16 : 32;
     const int KO = tco ? 128 : gj_outer_width<T>(b);
     cudaMemsetAsync(amax, 0, sizeof(T) * count, s);
-    k_maxabs<T><<<dim3(16, count), 256, 0, s>>>(mats, b, amax);
+    {
+        // enough CTAs to keep every SM streaming when a level has few blocks
+        // (the maximum is order-independent, so the split changes no bit)
+        const long long bb = (long long)b * b;
+        long long cx = std::max(16LL, (608LL + count - 1) / count);
+        cx = std::min(cx, std::max(1LL, bb / 1024));
+        cx = std::min(cx, 256LL);
+        k_maxabs<T><<<dim3((unsigned)cx, count), 256, 0, s>>>(mats, b, amax);
+    }
     count_launches(1);
     const size_t psmem = (size_t)b * KB * sizeof(T);
     auto kp = k_gj_panel<T, 512>;
