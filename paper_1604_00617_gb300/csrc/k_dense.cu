@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "acr_internal.h"
@@ -243,24 +244,45 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
 }
 
 // Register-resident panel step: thread t owns panel rows t, t+NT, ... (RPT of
-// them, KB values each, in registers).  Per pivot: block arg-max of the pivot
-// column, the owners of rows k and p publish them through shared memory, then
-// every thread applies the GJ step to its own rows.  Same arithmetic as
-// k_gj_panel.  The pivot loop is not unrolled (a straight-line copy of all KB
-// steps does not fit the instruction cache): instead every step leaves each
-// row rotated left by one column, so the pivot column is always v[.][0] and
-// register indices stay static; after KB steps the columns are back in order.
+// them, KB values each, in registers).  Per pivot, one barrier: every warp
+// reduces its rows to its best candidate (largest |value| in the pivot
+// column, lowest row on ties) and the owner of that row publishes the whole
+// row in the warp's slot, as the owner of row k publishes row k; after the
+// barrier every warp reduces the warps' candidates (the same total order, so
+// the same pivot as a block-wide arg-max) and reads the pivot row from the
+// winner's slot.  Slots alternate between two buffers by step parity: a
+// buffer is rewritten two steps later, after a barrier that every reader of
+// its previous contents has passed.  A row is stored from element VE - 1 on,
+// so that the elements 1.. that the update reads start a 16-byte vector.
+// Same pivots and the same arithmetic as k_gj_panel.  The pivot loop is not
+// unrolled (a straight-line copy of all KB steps does not fit the instruction
+// cache): instead every step leaves each row rotated left by one column, so
+// the pivot column is always v[.][0] and register indices stay static; after
+// KB steps the columns are back in order.
+// With a stash (non-NULL), the kernel ends with the work of k_gj_gather for
+// the columns [colA, colB) outside its panel (the only ones the update reads):
+// those columns are not written here, and the pivots are at hand.
 template <class T, int NT, int RPT, int KB>
 __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b, int k0,
                                                      int* __restrict__ pivs, int* __restrict__ info,
-                                                     const T* __restrict__ amax_in) {
-    __shared__ T rv[32];
-    __shared__ int ri[32];
-    __shared__ T sp[KB];
-    __shared__ T sk[KB];
+                                                     const T* __restrict__ amax_in, int colA, int colB,
+                                                     T* __restrict__ stash, int* __restrict__ slotmap) {
+    constexpr int NW = NT / 32;
+    constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte vector
+    constexpr int SH = VE - 1;               // row element c is stored at c + SH
+    constexpr int RL = KB + VE;              // stored row length, a multiple of VE
+    static_assert(KB % VE == 0 && NW <= 32, "panel layout");
+    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    __shared__ T rv[2][NW];
+    __shared__ int ri[2][NW];
+    __shared__ __align__(16) T srow[2][NW][RL];  // each warp's candidate row
+    __shared__ __align__(16) T skr[2][RL];       // row k
+    __shared__ int s_piv[KB];
     T* G = mats + (size_t)blockIdx.x * b * b;
     int* piv = pivs + (size_t)blockIdx.x * b;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 2 * NW * RL; i += NT) (&srow[0][0][0])[i] = T(0);
+    for (int i = tid; i < 2 * RL; i += NT) (&skr[0][0])[i] = T(0);
     T v[RPT][KB];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -270,9 +292,10 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     }
     const T tiny = T(16) * Lim<T>::eps() * amax_in[blockIdx.x];
     int first_bad = 0;
+    __syncthreads();  // the zeroed pads
 #pragma unroll 1
     for (int kk = 0; kk < KB; ++kk) {
-        const int k = k0 + kk;
+        const int k = k0 + kk, par = kk & 1;
         T val = T(-1);
         int idx = 0x7fffffff;
 #pragma unroll
@@ -283,45 +306,76 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
                 if (a > val) { val = a; idx = r; }
             }
         }
-        block_argmax(val, idx, rv, ri);
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        }
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int r = tid + i * NT;
+            if (r == idx) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) srow[par][warp][c + SH] = v[i][c];
+            }
+            if (r == k) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) skr[par][c + SH] = v[i][c];
+            }
+        }
+        if (lane == 0) { rv[par][warp] = val; ri[par][warp] = idx; }
+        __syncthreads();
+        val = lane < NW ? rv[par][lane] : T(-1);
+        idx = lane < NW ? ri[par][lane] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        }
         const int p = (idx < b) ? idx : k;
         const bool bad = !(val > tiny) || !tfinite(val);
         if (bad && first_bad == 0) first_bad = k + 1;
-        if (tid == 0) piv[k] = p;
+        if (tid == 0) {
+            piv[k] = p;
+            s_piv[kk] = p;
+        }
+        // the pivot row: the winning warp's slot (row k itself when p == k)
+        const T* spr = (p == k) ? skr[par] : srow[par][(p % NT) >> 5];
+        const T inv = bad ? T(1) : T(1) / spr[SH];
+        // row p takes row k's values; fi: each row's multiplier
+        T fi[RPT];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
-            if (r == p) {
+            if (r == p && r != k) {
 #pragma unroll
-                for (int c = 0; c < KB; ++c) sp[c] = v[i][c];
+                for (int c = 0; c < KB; ++c) v[i][c] = skr[par][c + SH];
             }
-            if (r == k) {
+            fi[i] = v[i][0] * inv;
+        }
+        // column c of this step is stored at c - 1 afterwards (the pivot
+        // column, c = 0, moves to KB - 1); the pivot row's elements 1.. are
+        // read a 16-byte vector at a time
 #pragma unroll
-                for (int c = 0; c < KB; ++c) sk[c] = v[i][c];
+        for (int m = 0; m < KB / VE; ++m) {
+            const V16 w = *reinterpret_cast<const V16*>(spr + VE * (m + 1));
+            const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) {
+                const int c = m * VE + e;
+                if (c < KB - 1) {
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) {
+                        const int r = tid + i * NT;
+                        v[i][c] = (r == k) ? wp[e] * inv : v[i][c + 1] - fi[i] * wp[e];
+                    }
+                }
             }
         }
-        __syncthreads();
-        const T inv = bad ? T(1) : T(1) / sp[0];
-        // column c of this step is stored at c - 1 afterwards (the pivot
-        // column, c = 0, moves to KB - 1)
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
-            if (r >= b) continue;
-            if (r == k) {
-#pragma unroll
-                for (int c = 0; c < KB - 1; ++c) v[i][c] = sp[c + 1] * inv;
-                v[i][KB - 1] = inv;
-            } else {
-                if (r == p) {
-#pragma unroll
-                    for (int c = 0; c < KB; ++c) v[i][c] = sk[c];
-                }
-                const T fi = v[i][0] * inv;
-#pragma unroll
-                for (int c = 0; c < KB - 1; ++c) v[i][c] = v[i][c + 1] - fi * sp[c + 1];
-                v[i][KB - 1] = -fi;
-            }
+            v[i][KB - 1] = (r == k) ? inv : -fi[i];
         }
     }
 #pragma unroll
@@ -333,6 +387,40 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
         }
     }
     if (tid == 0 && first_bad && info[blockIdx.x] == 0) info[blockIdx.x] = first_bad;
+    if (!stash) return;
+    // gather (see k_gj_gather): composed interchanges of the panel, slot map,
+    // and the moved rows of the other columns of [colA, colB) into the stash
+    extern __shared__ int gsh[];
+    int* perm = gsh;          // b
+    int* slot = perm + b;     // b
+    int* list = slot + b;     // KB
+    __shared__ int s_cnt;
+    for (int r = tid; r < b; r += NT) { perm[r] = r; slot[r] = -1; }
+    __syncthreads();  // also orders every s_piv write before the reads below
+    if (tid == 0) {
+        for (int kk = 0; kk < KB; ++kk) {
+            const int k = k0 + kk, p = s_piv[kk];
+            const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+            slot[k] = kk;
+        }
+        int cnt = 0;
+        for (int kk = 0; kk < KB; ++kk) {
+            const int p = s_piv[kk];
+            if (p >= k0 + KB && slot[p] < 0) { slot[p] = KB + cnt; list[cnt++] = p; }
+        }
+        s_cnt = cnt;
+    }
+    __syncthreads();
+    const int ns = KB + s_cnt;
+    for (int r = tid; r < b; r += NT) slotmap[(size_t)blockIdx.x * b + r] = slot[r];
+    T* st = stash + (size_t)blockIdx.x * 2 * KB * b;
+    const int nJ = (colB - colA) - KB;
+    for (int i = tid; i < ns * nJ; i += NT) {
+        const int sl = i % ns, jc = i / ns;
+        const int c = colA + jc < k0 ? colA + jc : colA + jc + KB;
+        const int r = sl < KB ? k0 + sl : list[sl - KB];
+        st[(size_t)sl * b + c] = G[perm[r] + (size_t)c * b];
+    }
 }
 
 // Two-kernel update for full parallelism over (row tile, column tile, block).
@@ -467,19 +555,40 @@ k_gj_update_vec(T* __restrict__ mats, int b, int k0, int kb, int colA, int colB,
     for (int i = 0; i < V; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-    for (int kq = 0; kq < kb; kq += BK) {
-        for (int i = tid; i < BM * BK; i += NT) {
-            const int r = i % BM, k = i / BM;
+    // the operands of a K chunk go through registers: all of a chunk's loads
+    // are issued at once, and the next chunk's while this one is multiplied
+    constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
+    static_assert(LA * NT == BM * BK && LB * NT == BK * BN, "tile loads");
+    T ra[LA], rb[LB];
+    auto fetch = [&](int kq) {
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            const int i = tid + u * NT, r = i % BM, k = i / BM;
             const int gr = row0 + r;
-            As[k][r] = (gr < b && kq + k < kb) ? G[gr + (size_t)(k0 + kq + k) * b] : T(0);
+            ra[u] = (gr < b && kq + k < kb) ? G[gr + (size_t)(k0 + kq + k) * b] : T(0);
         }
-        for (int i = tid; i < BK * BN; i += NT) {
-            const int j = i % BN, k = i / BN;
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = tid + u * NT, j = i % BN, k = i / BN;
             const int jc = j0 + j;
             const int c = colA + jc < k0 ? colA + jc : colA + jc + kb;
-            Bs[k][j] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
+            rb[u] = (jc < nJ && kq + k < kb) ? st[(size_t)(kq + k) * b + c] : T(0);
+        }
+    };
+    fetch(0);
+    for (int kq = 0; kq < kb; kq += BK) {
+#pragma unroll
+        for (int u = 0; u < LA; ++u) {
+            const int i = tid + u * NT;
+            As[i / BM][i % BM] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = tid + u * NT;
+            Bs[i / BN][i % BN] = rb[u];
         }
         __syncthreads();
+        if (kq + BK < kb) fetch(kq + BK);
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             const VT av = *reinterpret_cast<const VT*>(&As[k][ty * V]);
@@ -754,12 +863,15 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
     ensure_smem((const void*)kp, psmem);
     constexpr int BMU = sizeof(T) == 8 ? 64 : 128, TMU = sizeof(T) == 8 ? 4 : 8;
     // rank-kw update of the columns [cA, cB) outside [k0, k0 + kw)
-    auto update = [&](int k0, int kw, int cA, int cB) {
+    // (gathered: the panel kernel has filled the stash and the slot map)
+    auto update = [&](int k0, int kw, int cA, int cB, bool gathered) {
         const int nJ = (cB - cA) - kw;
         if (nJ <= 0) return;
-        k_gj_gather<T><<<dim3((cB - cA + 63) / 64, count), 256, (2 * (size_t)b + kw) * sizeof(int), s>>>(
-            mats, b, k0, kw, cA, cB, ws_piv, stash, slotmap);
-        count_launches(1);
+        if (!gathered) {
+            k_gj_gather<T><<<dim3((cB - cA + 63) / 64, count), 256, (2 * (size_t)b + kw) * sizeof(int), s>>>(
+                mats, b, k0, kw, cA, cB, ws_piv, stash, slotmap);
+            count_launches(1);
+        }
         const int tmu = (b + BMU - 1) / BMU, tnu = (nJ + BMU - 1) / BMU;
         if (b % (16 / (int)sizeof(T)) == 0) {
             constexpr int VV = 16 / sizeof(T), TNV = (BMU * BMU) / (256 * VV);
@@ -775,16 +887,25 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
         const int KOi = (b - K0) < KO ? (b - K0) : KO;
         for (int k0 = K0; k0 < K0 + KOi; k0 += KB) {
             const int kbi = (K0 + KOi - k0) < KB ? (K0 + KOi - k0) : KB;
-            if (kbi == KB && b <= 1024) {  // panel rows in registers
-                if (b <= 512) k_gj_panel_reg<T, 512, 1, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+            bool gathered = false;
+            if (kbi == KB && b <= 1024) {  // panel rows in registers, gather fused
+                const bool g = KOi > KB;
+                const size_t gsm = g ? (2 * (size_t)b + KB) * sizeof(int) : 0;
+                T* sts = g ? stash : nullptr;
+                if (b <= 512)
+                    k_gj_panel_reg<T, 512, 1, KB><<<count, 512, gsm, s>>>(mats, b, k0, ws_piv, info, amax, K0,
+                                                                          K0 + KOi, sts, slotmap);
                 // blocks above 512 rows: 512 threads with two rows each (fewer warps
                 // per barrier than one row per thread; the same pivots and bits)
-                else k_gj_panel_reg<T, 512, 2, KB><<<count, 512, 0, s>>>(mats, b, k0, ws_piv, info, amax);
+                else
+                    k_gj_panel_reg<T, 512, 2, KB><<<count, 512, gsm, s>>>(mats, b, k0, ws_piv, info, amax, K0,
+                                                                          K0 + KOi, sts, slotmap);
+                gathered = g;
             } else {
                 kp<<<count, 512, (size_t)b * kbi * sizeof(T), s>>>(mats, b, k0, kbi, ws_piv, info, amax);
             }
             count_launches(1);
-            update(k0, kbi, K0, K0 + KOi);  // inside the outer panel
+            update(k0, kbi, K0, K0 + KOi, gathered);  // inside the outer panel
         }
         // everything else, once per outer panel
         if constexpr (sizeof(T) == 4) {
@@ -801,7 +922,7 @@ static cudaError_t gj_blocked(T* mats, int b, int count, int* info, int* ws_piv,
                 continue;
             }
         }
-        update(K0, KOi, 0, b);
+        update(K0, KOi, 0, b, false);
     }
     const size_t usm = (size_t)UR * b * sizeof(T);
     if (usm <= 160 * 1024 && 2 * (size_t)b * sizeof(int) <= 160 * 1024) {
