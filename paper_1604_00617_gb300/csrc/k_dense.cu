@@ -250,15 +250,17 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
 // row in the warp's slot, as the owner of row k publishes row k; after the
 // barrier every warp reduces the warps' candidates (the same total order, so
 // the same pivot as a block-wide arg-max) and reads the pivot row from the
-// winner's slot.  Slots alternate between two buffers by step parity: a
-// buffer is rewritten two steps later, after a barrier that every reader of
-// its previous contents has passed.  A row is stored from element VE - 1 on,
-// so that the elements 1.. that the update reads start a 16-byte vector.
-// Same pivots and the same arithmetic as k_gj_panel.  The pivot loop is not
-// unrolled (a straight-line copy of all KB steps does not fit the instruction
-// cache): instead every step leaves each row rotated left by one column, so
-// the pivot column is always v[.][0] and register indices stay static; after
-// KB steps the columns are back in order.
+// winner's slot.  In FP32 the order is that of the key: the bits of |value|
+// without the sign bit, plus 1 (0: no candidate), reduced by redux.sync maxima
+// and minima.  Slots alternate
+// between two buffers by step parity: a buffer is rewritten two steps later,
+// after a barrier that every reader of its previous contents has passed.  A
+// row is stored with element 0 at VE - 1 and elements 1.. as 16-byte vectors
+// from VE on.  Same pivots and the same arithmetic as k_gj_panel.  The pivot
+// loop is not unrolled (a straight-line copy of all KB steps does not fit the
+// instruction cache): instead every step leaves each row rotated left by one
+// column, so the pivot column is always v[.][0] and register indices stay
+// static; after KB steps the columns are back in order.
 // With a stash (non-NULL), the kernel ends with the work of k_gj_gather for
 // the columns [colA, colB) outside its panel (the only ones the update reads):
 // those columns are not written here, and the pivots are at hand.
@@ -271,9 +273,11 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte vector
     constexpr int SH = VE - 1;               // row element c is stored at c + SH
     constexpr int RL = KB + VE;              // stored row length, a multiple of VE
+    constexpr bool F32 = sizeof(T) == 4;
     static_assert(KB % VE == 0 && NW <= 32, "panel layout");
-    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    using V16 = typename std::conditional<F32, float4, double2>::type;
     __shared__ T rv[2][NW];
+    __shared__ unsigned rkey[2][NW];
     __shared__ int ri[2][NW];
     __shared__ __align__(16) T srow[2][NW][RL];  // each warp's candidate row
     __shared__ __align__(16) T skr[2][RL];       // row k
@@ -281,8 +285,6 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     T* G = mats + (size_t)blockIdx.x * b * b;
     int* piv = pivs + (size_t)blockIdx.x * b;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 2 * NW * RL; i += NT) (&srow[0][0][0])[i] = T(0);
-    for (int i = tid; i < 2 * RL; i += NT) (&skr[0][0])[i] = T(0);
     T v[RPT][KB];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -292,7 +294,6 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
     }
     const T tiny = T(16) * Lim<T>::eps() * amax_in[blockIdx.x];
     int first_bad = 0;
-    __syncthreads();  // the zeroed pads
 #pragma unroll 1
     for (int kk = 0; kk < KB; ++kk) {
         const int k = k0 + kk, par = kk & 1;
@@ -306,31 +307,58 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
                 if (a > val) { val = a; idx = r; }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, val, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        unsigned wkey = 0;
+        if constexpr (F32) {
+            // (sign bit cleared: tabs leaves -0 negative, and -0 ties with +0)
+            const unsigned key = idx != 0x7fffffff ? (__float_as_uint((float)val) & 0x7fffffffu) + 1u : 0u;
+            wkey = __reduce_max_sync(0xffffffffu, key);
+            idx = (int)__reduce_min_sync(0xffffffffu, key == wkey ? (unsigned)idx : 0xffffffffu);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+            }
         }
+        // the warp's candidate row and row k: element 0, then 16-byte vectors
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
-            if (r == idx) {
+            const bool cand = r == idx, rowk = r == k;
+            if (cand || rowk) {
 #pragma unroll
-                for (int c = 0; c < KB; ++c) srow[par][warp][c + SH] = v[i][c];
-            }
-            if (r == k) {
+                for (int m = 0; m < KB / VE; ++m) {
+                    V16 w;
+                    T* wp = reinterpret_cast<T*>(&w);
 #pragma unroll
-                for (int c = 0; c < KB; ++c) skr[par][c + SH] = v[i][c];
+                    for (int e = 0; e < VE; ++e) wp[e] = (m * VE + e + 1 < KB) ? v[i][m * VE + e + 1] : T(0);
+                    if (cand) *reinterpret_cast<V16*>(&srow[par][warp][VE * (m + 1)]) = w;
+                    if (rowk) *reinterpret_cast<V16*>(&skr[par][VE * (m + 1)]) = w;
+                }
+                if (cand) srow[par][warp][SH] = v[i][0];
+                if (rowk) skr[par][SH] = v[i][0];
             }
         }
-        if (lane == 0) { rv[par][warp] = val; ri[par][warp] = idx; }
+        if (lane == 0) {
+            rv[par][warp] = val;
+            rkey[par][warp] = wkey;
+            ri[par][warp] = idx;
+        }
         __syncthreads();
-        val = lane < NW ? rv[par][lane] : T(-1);
-        idx = lane < NW ? ri[par][lane] : 0x7fffffff;
-        for (int o = 16; o > 0; o >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, val, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        if constexpr (F32) {
+            const unsigned k0v = lane < NW ? rkey[par][lane] : 0u;
+            const unsigned i0v = lane < NW ? (unsigned)ri[par][lane] : 0xffffffffu;
+            const unsigned bk = __reduce_max_sync(0xffffffffu, k0v);
+            idx = (int)__reduce_min_sync(0xffffffffu, k0v == bk ? i0v : 0xffffffffu);
+            val = bk ? (T)__uint_as_float(bk - 1u) : T(-1);
+        } else {
+            val = lane < NW ? rv[par][lane] : T(-1);
+            idx = lane < NW ? ri[par][lane] : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+            }
         }
         const int p = (idx < b) ? idx : k;
         const bool bad = !(val > tiny) || !tfinite(val);
@@ -348,14 +376,21 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
             if (r == p && r != k) {
+                v[i][0] = skr[par][SH];
 #pragma unroll
-                for (int c = 0; c < KB; ++c) v[i][c] = skr[par][c + SH];
+                for (int m = 0; m < KB / VE; ++m) {
+                    const V16 w = *reinterpret_cast<const V16*>(&skr[par][VE * (m + 1)]);
+                    const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+                    for (int e = 0; e < VE; ++e)
+                        if (m * VE + e + 1 < KB) v[i][m * VE + e + 1] = wp[e];
+                }
             }
             fi[i] = v[i][0] * inv;
         }
         // column c of this step is stored at c - 1 afterwards (the pivot
         // column, c = 0, moves to KB - 1); the pivot row's elements 1.. are
-        // read a 16-byte vector at a time
+        // read a 16-byte vector at a time.  Row k is redone below.
 #pragma unroll
         for (int m = 0; m < KB / VE; ++m) {
             const V16 w = *reinterpret_cast<const V16*>(spr + VE * (m + 1));
@@ -365,17 +400,26 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
                 const int c = m * VE + e;
                 if (c < KB - 1) {
 #pragma unroll
-                    for (int i = 0; i < RPT; ++i) {
-                        const int r = tid + i * NT;
-                        v[i][c] = (r == k) ? wp[e] * inv : v[i][c + 1] - fi[i] * wp[e];
-                    }
+                    for (int i = 0; i < RPT; ++i) v[i][c] = v[i][c + 1] - fi[i] * wp[e];
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
             const int r = tid + i * NT;
-            v[i][KB - 1] = (r == k) ? inv : -fi[i];
+            if (r == k) {
+#pragma unroll
+                for (int m = 0; m < KB / VE; ++m) {
+                    const V16 w = *reinterpret_cast<const V16*>(spr + VE * (m + 1));
+                    const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+                    for (int e = 0; e < VE; ++e)
+                        if (m * VE + e < KB - 1) v[i][m * VE + e] = wp[e] * inv;
+                }
+                v[i][KB - 1] = inv;
+            } else {
+                v[i][KB - 1] = -fi[i];
+            }
         }
     }
 #pragma unroll
