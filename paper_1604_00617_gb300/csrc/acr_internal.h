@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -282,6 +283,32 @@ __device__ __forceinline__ T jacobi_tan(T zeta) {
     const T az = fabs(zeta);
     const T root = az > T(1) ? az * sqrt(T(1) + (T(1) / az) * (T(1) / az)) : sqrt(T(1) + az * az);
     return (zeta >= T(0) ? T(1) : T(-1)) / (az + root);
+}
+// Arg-max key of an FP32 pivot candidate whose magnitude a was taken as
+// x < 0 ? -x : x (so -0 stays -0; a is never NaN, which no comparison
+// selects): the bits of a without the sign bit, plus 1; 0 for no candidate.
+// Non-negative floats are ordered as their bit patterns, so the largest key
+// is the largest magnitude, -0 ties with +0 as in a float comparison, and a
+// tie goes to the lowest row in both orders.  gj_pivot_mag inverts a nonzero
+// key.
+__host__ __device__ __forceinline__ unsigned gj_pivot_key(float a, bool valid) {
+#ifdef __CUDA_ARCH__
+    const unsigned u = __float_as_uint(a);
+#else
+    unsigned u;
+    memcpy(&u, &a, sizeof(u));
+#endif
+    return valid ? (u & 0x7fffffffu) + 1u : 0u;
+}
+__host__ __device__ __forceinline__ float gj_pivot_mag(unsigned key) {
+    const unsigned u = key - 1u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float a;
+    memcpy(&a, &u, sizeof(a));
+    return a;
+#endif
 }
 }  // namespace acr
 #endif

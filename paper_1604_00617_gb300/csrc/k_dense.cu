@@ -250,9 +250,8 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
 // row in the warp's slot, as the owner of row k publishes row k; after the
 // barrier every warp reduces the warps' candidates (the same total order, so
 // the same pivot as a block-wide arg-max) and reads the pivot row from the
-// winner's slot.  In FP32 the order is that of the key: the bits of |value|
-// without the sign bit, plus 1 (0: no candidate), reduced by redux.sync maxima
-// and minima.  Slots alternate
+// winner's slot.  In FP32 the order is that of gj_pivot_key (the same order
+// as the float comparison), reduced by redux.sync maxima and minima.  Slots alternate
 // between two buffers by step parity: a buffer is rewritten two steps later,
 // after a barrier that every reader of its previous contents has passed.  A
 // row is stored with element 0 at VE - 1 and elements 1.. as 16-byte vectors
@@ -309,8 +308,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
         }
         unsigned wkey = 0;
         if constexpr (F32) {
-            // (sign bit cleared: tabs leaves -0 negative, and -0 ties with +0)
-            const unsigned key = idx != 0x7fffffff ? (__float_as_uint((float)val) & 0x7fffffffu) + 1u : 0u;
+            const unsigned key = gj_pivot_key((float)val, idx != 0x7fffffff);
             wkey = __reduce_max_sync(0xffffffffu, key);
             idx = (int)__reduce_min_sync(0xffffffffu, key == wkey ? (unsigned)idx : 0xffffffffu);
         } else {
@@ -350,7 +348,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(T* __restrict__ mats, int b
             const unsigned i0v = lane < NW ? (unsigned)ri[par][lane] : 0xffffffffu;
             const unsigned bk = __reduce_max_sync(0xffffffffu, k0v);
             idx = (int)__reduce_min_sync(0xffffffffu, k0v == bk ? i0v : 0xffffffffu);
-            val = bk ? (T)__uint_as_float(bk - 1u) : T(-1);
+            val = bk ? (T)gj_pivot_mag(bk) : T(-1);
         } else {
             val = lane < NW ? rv[par][lane] : T(-1);
             idx = lane < NW ? ri[par][lane] : 0x7fffffff;
