@@ -319,6 +319,27 @@ def test_tensor_core_inversion_with_interchanges(lib, n, b):
     assert relerr(Xr, oracle.bcr_solve(A, D, C, F)) <= 1e-9
 
 
+@pytest.mark.parametrize("n,b", [(3, 300), (2, 520)])
+def test_fp32_blocked_inversion_ragged(lib, n, b):
+    """FP32 blocks above the shared-memory limit whose size is not a multiple
+    of the 32-column panel: register panels (one row per thread up to 512
+    rows, two above) that gather for their update themselves, then a narrow
+    last panel through the generic panel kernel and the separate gather, with
+    rows interchanged everywhere.  Refined to the oracle."""
+    rng = np.random.default_rng(11 * b + n)
+    A, D, C = syn.random_blocks(n, b, seed=3 * b + n)
+    for i in range(n):
+        D[i] = D[i][rng.permutation(b)]
+    F = rng.uniform(-1, 1, (n * b, 2))
+    h = factor(lib, A, D, C, prec=2)
+    try:
+        X, res, it = solve(lib, h, F)
+    finally:
+        lib.acr_free(h)
+    assert (res <= 1e-8).all()
+    assert relerr(X, oracle.bcr_solve(A, D, C, F)) <= 1e-9
+
+
 @pytest.mark.parametrize("idx,n", [(1, 128), (2, 256), (3, 256)])
 def test_pde_tensor_core_refinement(lib, idx, n):
     P = syn.make_config(idx, n)
