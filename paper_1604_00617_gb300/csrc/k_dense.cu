@@ -251,15 +251,15 @@ __global__ void __launch_bounds__(NT) k_gj_panel(T* __restrict__ mats, int b, in
 // barrier every warp reduces the warps' candidates (the same total order, so
 // the same pivot as a block-wide arg-max) and reads the pivot row from the
 // winner's slot.  In FP32 the order is that of gj_pivot_key (the same order
-// as the float comparison), reduced by redux.sync maxima and minima.  Slots alternate
-// between two buffers by step parity: a buffer is rewritten two steps later,
-// after a barrier that every reader of its previous contents has passed.  A
-// row is stored with element 0 at VE - 1 and elements 1.. as 16-byte vectors
-// from VE on.  Same pivots and the same arithmetic as k_gj_panel.  The pivot
-// loop is not unrolled (a straight-line copy of all KB steps does not fit the
-// instruction cache): instead every step leaves each row rotated left by one
-// column, so the pivot column is always v[.][0] and register indices stay
-// static; after KB steps the columns are back in order.
+// as the float comparison), reduced by redux.sync maxima and minima.  Slots
+// alternate between two buffers by step parity: a buffer is rewritten two
+// steps later, after a barrier that every reader of its previous contents has
+// passed.  A row is stored with element 0 at VE - 1 and elements 1.. as
+// 16-byte vectors from VE on.  Same pivots and the same arithmetic as
+// k_gj_panel.  The pivot loop is not unrolled (a straight-line copy of all KB
+// steps does not fit the instruction cache): instead every step leaves each
+// row rotated left by one column, so the pivot column is always v[.][0] and
+// register indices stay static; after KB steps the columns are back in order.
 // With a stash (non-NULL), the kernel ends with the work of k_gj_gather for
 // the columns [colA, colB) outside its panel (the only ones the update reads):
 // those columns are not written here, and the pivots are at hand.
